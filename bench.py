@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the D2Q9 bounce-back solver with per-step forces on one GB300.
+
+One bench step is one lattice time step of the whole hot path: the fused
+collide-stream kernel over the grid (bounce-back, inlet/outlet, DRTT partials)
+plus the link kernel (momentum exchange A, A', B and DRTT), forces of every
+scheme recorded on the device.  Default workload: 4096 x 2048 NACA0012, chord
+256 at 4 degrees, Re 1000, FP32 storage.  The population arrays (2 x 302 MB)
+exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload (weak scaling, no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f32dev": 72, "f16dev": 36}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2210_10377_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel][workload]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def naca_mask_device(w):
+    from paper_2210_10377_gb300 import binding
+    return binding.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
+
+
+def time_steps(torch, lat, steps):
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def kernel_roofline(torch, lat, w, storage, steps, peak):
+    lat.set_kernel_timing(True)
+    lat.kernel_times(reset=True)
+    lat.step(steps)
+    kt = lat.kernel_times(reset=True)
+    lat.set_kernel_timing(False)
+    ms, n = kt["collide_stream"]
+    avg_s = ms / n / 1e3
+    algo = BYTES_PER_UPDATE[storage] * w.nodes
+    achieved = algo / avg_s / 1e9
+    return {"achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "avg_launch_us": avg_s * 1e6, "algorithmic_bytes": algo,
+            "link_kernel_us": kt["link_force"][0] / kt["link_force"][1] * 1e3}
+
+
+def variant(torch, binding, w, storage, steps, peak, device):
+    mask = naca_mask_device(w)
+    lat = binding.Lattice(mask, w.tau, w.u_in, storage=storage, device=device)
+    lat.step(20)
+    ms = time_steps(torch, lat, steps)
+    rl = kernel_roofline(torch, lat, w, storage, min(steps, 500), peak)
+    lat.close()
+    mlups = w.nodes * steps / (ms / 1e3) / 1e6
+    return {"workload": w.name if storage == w.storage else w.name + "_as_" + storage,
+            "storage": storage, "MLUPS": round(mlups, 1), "steps": steps,
+            "ms_per_step": ms / steps, "bytes_per_update": BYTES_PER_UPDATE[storage],
+            "collide_stream_GBps": round(rl["achieved"], 1),
+            "frac_of_measured_hbm": round(rl["frac"], 4)}
+
+
+def oracle_sample(w, seconds, mask=None):
+    """The FP64 CPU oracle on the same workload, stepped until `seconds` pass."""
+    import oracle
+    if mask is None:
+        mask = oracle.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
+    sim = oracle.Sim(mask, w.tau, w.u_in)
+    sim.step(1)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return w.nodes * steps / el / 1e6, steps, el
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2210_10377_gb300 import inputs
+    w = inputs.LARGE_F32
+    budget = min(120.0, max(10.0, 0.5 * (a.steps + a.warmup)))
+    mlups, steps, el = oracle_sample(w, budget)
+    line = {"metric": "MLUPS", "value": round(mlups, 3), "unit": "MLUPS", "impl": "reference",
+            "n_gpus": a.gpus, "steps": steps, "warmup": 1, "ms_per_step": el / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "chord": w.chord,
+                       "alpha_deg": w.alpha_deg, "re": w.re, "tau": w.tau},
+            "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "FP64 oracle, %d steps of the full %dx%d grid after one "
+                                       "warm-up step (time-bounded at %.0f s)"
+                                       % (steps, w.nx, w.ny, budget)},
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+
+    from paper_2210_10377_gb300 import binding, inputs
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    binding.lib()
+    w = inputs.LARGE_F32
+    storage = w.storage
+    peak, peak_kind = measured_peaks()
+
+    # -- device throughput: inputs resident, K steps between barriers
+    mask = naca_mask_device(w)
+    lat = binding.Lattice(mask, w.tau, w.u_in, storage=storage, device=local)
+    lat.step(a.warmup)
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lat.launch_count
+    ms = time_steps(torch, lat, a.steps)
+    launches = lat.launch_count - launches0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * w.nodes * a.steps / (ms / 1e3) / 1e6
+    rl = kernel_roofline(torch, lat, w, storage, min(a.steps, 2000), peak)
+    lat.close()
+
+    # -- end to end through the public API from pinned host buffers
+    pm = torch.empty((w.ny, w.nx), dtype=torch.uint8, pin_memory=True)
+    pm.numpy()[:] = mask
+    fx = torch.empty(a.steps, dtype=torch.float64, pin_memory=True)
+    fy = torch.empty(a.steps, dtype=torch.float64, pin_memory=True)
+    pop = torch.empty((9, w.ny, w.nx), dtype=torch.float64, pin_memory=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat2 = binding.Lattice(pm.numpy(), w.tau, w.u_in, storage=storage, device=local)
+    lat2.step(a.steps)
+    for s in ("A", "B", "DRTT", "A_RTT"):
+        gx, gy = lat2.force_series(s)
+        fx.numpy()[:] = gx
+        fy.numpy()[:] = gy
+    lat2.populations(out=pop.numpy())
+    lat2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * w.nodes * a.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": round((w.nodes + 8) / a.steps, 3),
+           "d2h_bytes_per_step": round((4 * 2 * 8 * a.steps + 9 * 8 * w.nodes) / a.steps, 3),
+           "includes": "lbm_create from a pinned host mask, lbm_step(K), force series of all "
+                       "four schemes read back, final populations read back, lbm_destroy"}
+
+    variants = None
+    if not a.no_variants and rank == 0:
+        variants = [variant(torch, binding, w, "f64", 1000, peak, local),
+                    variant(torch, binding, w, "f32dev", 4000, peak, local),
+                    variant(torch, binding, w, "f16dev", 4000, peak, local),
+                    variant(torch, binding, inputs.PRECISION, "f16dev", 2000, peak, local),
+                    variant(torch, binding, inputs.PRECISION, "f32dev", 1000, peak, local)]
+
+    cpu = None
+    if rank == 0 and world == 1:
+        mlups, steps, el = oracle_sample(w, a.cpu_seconds, mask)
+        cpu = {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle, %d steps of the full %dx%d grid after one warm-up step "
+                         "(%.1f s)" % (steps, w.nx, w.ny, el)}
+
+    if rank == 0:
+        traffic = ncu_traffic("collide_stream", w.name)
+        line = {
+            "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "chord": w.chord,
+                       "thickness": w.thickness, "alpha_deg": w.alpha_deg, "re": w.re,
+                       "tau": w.tau, "u_in": w.u_in, "storage": storage,
+                       "forces_per_step": ["MEA_A", "MEA_B", "DRTT", "MEA_A_RTT"],
+                       "l2": "inputs larger than L2 (2 x %.0f MB populations)"
+                             % (9 * 4 * w.nodes / 1e6),
+                       "parallelism": "replicas%d" % world},
+            "roofline": {"bound": "hbm", "achieved": round(rl["achieved"], 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(rl["frac"], 4), "traffic": traffic,
+                         "kernel": "k_collide_stream<f32>", "peak_source": peak_kind,
+                         "avg_launch_us": round(rl["avg_launch_us"], 2),
+                         "algorithmic_bytes_per_launch": rl["algorithmic_bytes"],
+                         "link_kernel_us": round(rl["link_kernel_us"], 2)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

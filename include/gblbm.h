@@ -1,0 +1,201 @@
+/*
+ * gblbm.h -- C ABI of the gblbm library: a D2Q9 lattice Boltzmann solver with
+ * halfway bounce-back on a voxelised rigid body, and the body force evaluated
+ * every step by three schemes, after Kaushal, Succi & Ansumali, "Flow force
+ * calculation in Lattice Boltzmann Method" (arXiv:2210.10377).
+ *
+ * Everything a call computes runs in the library's CUDA kernels (sm_103a).
+ * There is no CPU fallback: without a usable GPU every compute call returns
+ * LBM_ECUDA.
+ *
+ * Notation used below (Section II of the paper):
+ *   nodes (x, y), 0 <= x < nx, 0 <= y < ny, node index n = y*nx + x;
+ *   D2Q9 directions 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
+ *                   5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1);
+ *   weights 4/9, 1/9 (1..4), 1/36 (5..8); theta0 = 1/3;
+ *   f(x, t) pre-collision populations, ft(x, t) post-collision (Eq. CollideAdv);
+ *   ft = f + (feq - f)/tau, i.e. the paper's 2*beta equals 1/tau and the
+ *   kinematic viscosity is (tau - 1/2)/3 in lattice units.
+ *   Population arrays crossing this ABI are double [9][ny][nx], row-major.
+ *
+ * Ownership: every pointer argument is caller-owned host memory, read or
+ * written only during the call.  Device memory is owned by the handle and
+ * comes from the allocator in lbm_bc (cudaMalloc when none is given).
+ * A handle is not thread-safe; distinct handles are independent.
+ * Errors: every call returns an lbm_status; lbm_last_error(h) gives a message
+ * (lbm_last_error(NULL) for calls that have no handle).  No C++ exception and
+ * no process exit crosses this ABI.
+ */
+#ifndef GBLBM_H
+#define GBLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* an argument is out of range (message says which) */
+    LBM_ENOMEM = 2,    /* the allocator returned NULL */
+    LBM_ECUDA = 3,     /* a CUDA call failed (no device, launch error, ...) */
+    LBM_EUNSTABLE = 4, /* a step produced rho <= 0 or NaN (first step index in the message) */
+    LBM_ETIMEOUT = 5,  /* reserved for bounded device waits */
+    LBM_ESTATE = 6     /* the request needs a state that does not exist yet */
+} lbm_status;
+
+typedef enum {
+    /* equilibrium inlet at x = 0 (ft = feq(rho0, (u_in(y), 0))), zero-gradient
+     * outlet at x = nx-1 (f(nx-1, y) = f(nx-2, y) after streaming), periodic y */
+    LBM_BC_CHANNEL = 0,
+    /* periodic in x and y */
+    LBM_BC_PERIODIC = 1
+} lbm_bc_kind;
+
+typedef enum {
+    LBM_F64 = 0,     /* populations stored and collided in FP64 */
+    LBM_F32 = 1,     /* stored and collided in FP32 */
+    LBM_F32_DEV = 2, /* FP32 storage of g_i = f_i - w_i rho0, FP32 collision */
+    LBM_F16_DEV = 3  /* FP16 storage of g_i = f_i - w_i rho0, FP32 collision */
+} lbm_storage;
+
+typedef enum {
+    /* Momentum exchange, Eq. (MEA): F = sum over fluid-solid links (x_f, i) of
+     * c_i [f_i(x_f) + f_opp(i)(x_f)], both on the pre-collision state f(x_f, t)
+     * (algorithm A of Fig. basicLadd). */
+    LBM_FORCE_MEA_A = 0,
+    /* Algorithm B, Eq. (rtt5) with bounce-back: F = 2 sum c_i ft_i(x_f, t). */
+    LBM_FORCE_MEA_B = 1,
+    /* Discrete Reynolds transport theorem, Eq. (rtt7) (second form) and the
+     * Appendix: F(t) = J(t) - J(t+1) + gained(t) - lost(t) over the control
+     * volume box.  Needs J(t+1), i.e. one step beyond t. */
+    LBM_FORCE_DRTT = 2,
+    /* Eq. (rtt4) read literally for algorithm A: lost momentum with f_i(x_f, t),
+     * gained momentum with the bounced ft_i(x_f, t). Diagnostic. */
+    LBM_FORCE_MEA_A_RTT = 3
+} lbm_scheme;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns a device pointer (16-byte aligned at least) or NULL; stream is
+ * the handle's stream.  free releases a pointer from alloc. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbm_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    int kind;             /* lbm_bc_kind */
+    int storage;          /* lbm_storage */
+    double rho0;          /* reference density: inlet density, deviation base (1.0) */
+    double body_force[2]; /* uniform body force g: ft_i += 3 w_i c_i.g (test set-ups) */
+    int cv[4];            /* DRTT control volume, inclusive {x0, x1, y0, y1};
+                             cv[0] < 0 selects the default box (see lbm_create) */
+    int record_series;    /* 1: keep forces of every step; 0: only the last two */
+    void *cuda_stream;    /* cudaStream_t for all work of the handle; NULL = legacy default */
+    lbm_alloc_fn alloc;   /* NULL: cudaMalloc / cudaFree */
+    lbm_free_fn free;
+    void *alloc_user;
+} lbm_bc;
+
+/* Fill *bc with defaults: channel, FP32, rho0 = 1, no body force, default
+ * control volume, record_series = 1, default stream, cudaMalloc. */
+void lbm_bc_default(lbm_bc *bc);
+
+/* Create a solver on an nx x ny grid.
+ *   mask     uint8 [ny][nx], nonzero = solid node (x_s), zero = fluid (x_f);
+ *            the halfway bounce-back wall sits half-way along every
+ *            fluid-solid link (Section II, Fig. basicLadd).
+ *   tau      lattice relaxation time, > 0.5.
+ *   u_in     inlet velocity, n_u_in values: 1 (uniform) or ny (per row y).
+ *   bc       boundary set-up, storage, control volume, stream, allocator.
+ * Initial state (t = 0): f = feq(rho0, (u_in(y), 0)) on every fluid node.
+ * Default control volume: the solid nodes' bounding box widened by
+ * max(4, ceil(w/4)) nodes per side (w = box width in x), clipped in x to
+ * [1, nx-2] in a channel; a range that would touch a periodic edge becomes the
+ * whole period.
+ * EINVAL: nx < 4, ny < 3, 8*nx*ny >= 2^31, tau <= 0.5, non-finite input, bad
+ * kind/storage/n_u_in, rho0 <= 0, a solid node in columns 0, 1, nx-2, nx-1 of a
+ * channel, or a control volume that touches the inlet/outlet column or
+ * straddles a periodic edge (it must lie within [1, n-2] or span [0, n-1]).
+ * ENOMEM / ECUDA as named.  On success *out receives the handle. */
+lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const double *u_in,
+                      int n_u_in, const lbm_bc *bc, lbm_ctx **out);
+
+/* Advance n >= 0 steps.  Each step t -> t+1 runs, in this order, the fused
+ * pull-stream + bounce-back + inlet/outlet + BGK collision kernel (which also
+ * accumulates J(t) and the control-volume fluxes), then the link kernel (MEA
+ * A, A', B of step t and DRTT of step t-1).  Blocks until the work is done.
+ * EUNSTABLE if any step produced rho <= 0 or NaN (the state then holds the
+ * result after all n steps). */
+lbm_status lbm_step(lbm_ctx *h, int n);
+
+/* Force on the body (+x downstream) of the last completed step t = T-1
+ * (the transition T-1 -> T) for one lbm_scheme.  ESTATE before the first step. */
+lbm_status lbm_force(lbm_ctx *h, int scheme, double *fx, double *fy);
+
+/* Forces of steps [first, first+count) for one scheme into fx[count], fy[count].
+ * EINVAL if the range is not kept (record_series = 0 keeps the last two). */
+lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, double *fx,
+                            double *fy);
+
+/* Pre-collision populations f(x, T) as double [9][ny][nx]; solid nodes read 0.
+ * For deviation storage the base w_i rho0 is added back in FP64. */
+lbm_status lbm_populations(lbm_ctx *h, double *out);
+
+/* Replace f(x, T) by in[9][ny][nx] (fluid nodes; solid entries are ignored),
+ * rounded to the storage precision.  The step count is kept. */
+lbm_status lbm_set_populations(lbm_ctx *h, const double *in);
+
+/* The fluid-solid link list, built on the device: entries n*8 + (i-1) for every
+ * fluid node n and direction i = 1..8 whose neighbour n + c_i (y periodic, x
+ * periodic only for LBM_BC_PERIODIC) is solid, in ascending order.  Writes at
+ * most cap entries to out and the total count to *count. */
+lbm_status lbm_links(lbm_ctx *h, int32_t *out, long cap, long *count);
+
+/* The control volume in use, inclusive {x0, x1, y0, y1}. */
+lbm_status lbm_control_volume(lbm_ctx *h, int *cv);
+
+/* Voxelise a NACA 4-digit symmetric section on the device.  Half-thickness
+ *   y_t(s) = 5 t C [0.2969 sqrt(s) - 0.1260 s - 0.3516 s^2 + 0.2843 s^3 - a4 s^4],
+ * s = xi/C, a4 = 0.1015 (closed_te = 0) or 0.1036 (closed_te = 1); mid-chord at
+ * (xc, yc); alpha > 0 nose-up:
+ *   xi = (x - xc) cos(alpha) - (y - yc) sin(alpha) + C/2,
+ *   eta = (x - xc) sin(alpha) + (y - yc) cos(alpha);
+ * node solid iff 0 <= xi <= C and |eta| <= y_t(xi/C).  cos and sin are taken on
+ * the host of alpha = alpha_deg * pi / 180; the predicate is evaluated on the
+ * device in FP64 with round-to-nearest operations in the order written above.
+ * (The paper names the NACA0012 section, Section V, but not its formula.)
+ * out: uint8 [ny][nx].  EINVAL for non-positive sizes, chord or thickness. */
+lbm_status lbm_naca_mask(int nx, int ny, double chord, double thickness, double alpha_deg,
+                         double xc, double yc, int closed_te, uint8_t *out);
+
+/* Number of completed steps T. */
+long lbm_steps_done(const lbm_ctx *h);
+
+/* Number of fluid-solid links. */
+long lbm_num_links(const lbm_ctx *h);
+
+/* Kernel timing for measurements: while on, lbm_step launches each kernel
+ * separately (no CUDA graph) between CUDA events on the handle's stream and
+ * accumulates device time per kernel.  lbm_kernel_times writes, for
+ * k = 0 (collide-stream) and k = 1 (link force), total milliseconds ms[k] and
+ * launch counts launches[k] since the last reset; reset = 1 clears them. */
+lbm_status lbm_set_kernel_timing(lbm_ctx *h, int on);
+lbm_status lbm_kernel_times(lbm_ctx *h, double *ms, long *launches, int reset);
+
+/* Kernel launches made by the handle since creation (all kernels). */
+long lbm_launch_count(const lbm_ctx *h);
+
+/* Message of the last failed call on h (or of the calling thread when h is NULL). */
+const char *lbm_last_error(const lbm_ctx *h);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void lbm_destroy(lbm_ctx *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBLBM_H */

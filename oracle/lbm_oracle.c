@@ -169,9 +169,11 @@ long oracle_links(const unsigned char *mask, int nx, int ny, int periodic_x, int
 
 /* Default control volume (Appendix: a rectangle around the body): the bounding
  * box of the solid nodes, widened by m = max(4, ceil(w/4)) nodes on each side,
- * w = bounding-box width in x, then clipped to x in [1, nx-2] (channel) or
- * [0, nx-1] (periodic) and y in [0, ny-1].  With no solid node the box is the
- * whole clipped domain.  Box is inclusive: cv = {x0, x1, y0, y1}. */
+ * w = bounding-box width in x.  In a channel the x-range is then clipped to
+ * [1, nx-2], so the inlet and outlet columns stay outside.  In a periodic
+ * direction a widened range that would reach the first or last node becomes the
+ * whole period instead (a box never straddles a periodic edge).  With no solid
+ * node the box is the whole allowed domain.  Inclusive: cv = {x0, x1, y0, y1}. */
 void oracle_auto_cv(const unsigned char *mask, int nx, int ny, int periodic_x, int *cv)
 {
     int xmin = nx, xmax = -1, ymin = ny, ymax = -1;
@@ -183,18 +185,28 @@ void oracle_auto_cv(const unsigned char *mask, int nx, int ny, int periodic_x, i
                 if (y < ymin) ymin = y;
                 if (y > ymax) ymax = y;
             }
-    int lo = periodic_x ? 0 : 1, hi = periodic_x ? nx - 1 : nx - 2;
     if (xmax < 0) {
-        cv[0] = lo; cv[1] = hi; cv[2] = 0; cv[3] = ny - 1;
+        cv[0] = periodic_x ? 0 : 1;
+        cv[1] = periodic_x ? nx - 1 : nx - 2;
+        cv[2] = 0;
+        cv[3] = ny - 1;
         return;
     }
     int w = xmax - xmin + 1;
     int m = (w + 3) / 4;
     if (m < 4) m = 4;
-    cv[0] = xmin - m < lo ? lo : xmin - m;
-    cv[1] = xmax + m > hi ? hi : xmax + m;
-    cv[2] = ymin - m < 0 ? 0 : ymin - m;
-    cv[3] = ymax + m > ny - 1 ? ny - 1 : ymax + m;
+    int x0 = xmin - m, x1 = xmax + m, y0 = ymin - m, y1 = ymax + m;
+    if (periodic_x) {
+        if (x0 < 1 || x1 > nx - 2) { x0 = 0; x1 = nx - 1; }
+    } else {
+        if (x0 < 1) x0 = 1;
+        if (x1 > nx - 2) x1 = nx - 2;
+    }
+    if (y0 < 1 || y1 > ny - 2) { y0 = 0; y1 = ny - 1; }
+    cv[0] = x0;
+    cv[1] = x1;
+    cv[2] = y0;
+    cv[3] = y1;
 }
 
 /* ------------------------------- the solver ------------------------------- */

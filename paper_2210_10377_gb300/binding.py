@@ -1,0 +1,255 @@
+"""Python binding of libgblbm.so (ctypes): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels.  PyTorch supplies
+the CUDA stream and, through the allocator hook of ``lbm_bc``, device memory
+from its caching allocator.  Importing this module raises if the library has
+not been built; there is no fallback implementation.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+CHANNEL, PERIODIC = 0, 1
+F64, F32, F32_DEV, F16_DEV = 0, 1, 2, 3
+STORAGE = {"f64": F64, "f32": F32, "f32dev": F32_DEV, "f16dev": F16_DEV}
+MEA_A, MEA_B, DRTT, MEA_A_RTT = 0, 1, 2, 3
+SCHEMES = {"A": MEA_A, "B": MEA_B, "DRTT": DRTT, "A_RTT": MEA_A_RTT}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT",
+          6: "ESTATE"}
+HEADER = os.path.join(_build.ROOT, "include", "gblbm.h")
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class lbm_bc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("storage", C.c_int), ("rho0", C.c_double),
+                ("body_force", C.c_double * 2), ("cv", C.c_int * 4),
+                ("record_series", C.c_int), ("cuda_stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libgblbm.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libgblbm.so is not built (%s); run __graft_entry__.build() or "
+                           "python -m paper_2210_10377_gb300.build" % _build.LIB)
+    L = C.CDLL(_build.LIB)
+    vp, dp, ip, lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_long)
+    L.lbm_bc_default.argtypes = [C.POINTER(lbm_bc)]
+    L.lbm_bc_default.restype = None
+    L.lbm_create.argtypes = [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_double, dp, C.c_int,
+                             C.POINTER(lbm_bc), C.POINTER(vp)]
+    L.lbm_step.argtypes = [vp, C.c_int]
+    L.lbm_force.argtypes = [vp, C.c_int, dp, dp]
+    L.lbm_force_series.argtypes = [vp, C.c_int, C.c_long, C.c_long, dp, dp]
+    L.lbm_populations.argtypes = [vp, dp]
+    L.lbm_set_populations.argtypes = [vp, dp]
+    L.lbm_links.argtypes = [vp, C.POINTER(C.c_int32), C.c_long, lp]
+    L.lbm_control_volume.argtypes = [vp, ip]
+    L.lbm_naca_mask.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                C.c_double, C.c_double, C.c_int, C.POINTER(C.c_uint8)]
+    L.lbm_steps_done.argtypes = [vp]
+    L.lbm_steps_done.restype = C.c_long
+    L.lbm_num_links.argtypes = [vp]
+    L.lbm_num_links.restype = C.c_long
+    L.lbm_set_kernel_timing.argtypes = [vp, C.c_int]
+    L.lbm_kernel_times.argtypes = [vp, dp, lp, C.c_int]
+    L.lbm_launch_count.argtypes = [vp]
+    L.lbm_launch_count.restype = C.c_long
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    for name in ("lbm_create", "lbm_step", "lbm_force", "lbm_force_series", "lbm_populations",
+                 "lbm_set_populations", "lbm_links", "lbm_control_volume", "lbm_naca_mask",
+                 "lbm_set_kernel_timing", "lbm_kernel_times"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def header_functions(path=HEADER):
+    """Names of the functions declared in include/gblbm.h."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)) - {"lbm_alloc_fn", "lbm_free_fn"})
+
+
+def _check(rc, h=None):
+    if rc != 0:
+        msg = lib().lbm_last_error(h)
+        raise LbmError(rc, msg.decode() if msg else "")
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def naca_mask(nx, ny, chord, thickness, alpha_deg, xc, yc, closed_te=False):
+    """NACA 4-digit section voxelised on the device; uint8 [ny][nx], 1 = solid."""
+    out = np.zeros((ny, nx), np.uint8)
+    _check(lib().lbm_naca_mask(int(nx), int(ny), float(chord), float(thickness),
+                               float(alpha_deg), float(xc), float(yc), int(closed_te),
+                               out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return out
+
+
+class _TorchAllocator:
+    """Device memory for the library from torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, stream, user):
+        try:
+            p = self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0)
+        except Exception:
+            return None
+        self.live[p] = nbytes
+        return p
+
+    def _free(self, ptr, user):
+        if ptr in self.live:
+            del self.live[ptr]
+            self.torch.cuda.caching_allocator_delete(ptr)
+
+
+class Lattice:
+    """One solver handle (lbm_create ... lbm_destroy)."""
+
+    def __init__(self, mask, tau, u_in, *, kind=CHANNEL, storage="f32", rho0=1.0,
+                 body_force=(0.0, 0.0), cv=None, record_series=True, stream=None,
+                 torch_alloc=True, device=0):
+        import torch
+        L = lib()
+        self.mask = np.ascontiguousarray(mask, np.uint8)
+        self.ny, self.nx = self.mask.shape
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        u = np.ascontiguousarray(np.atleast_1d(np.asarray(u_in, np.float64)))
+        bc = lbm_bc()
+        L.lbm_bc_default(C.byref(bc))
+        bc.kind = int(kind)
+        bc.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        bc.rho0 = float(rho0)
+        bc.body_force[0], bc.body_force[1] = float(body_force[0]), float(body_force[1])
+        if cv is not None:
+            for k in range(4):
+                bc.cv[k] = int(cv[k])
+        bc.record_series = int(bool(record_series))
+        bc.cuda_stream = self.stream.cuda_stream
+        self._alloc = _TorchAllocator(device) if torch_alloc else None
+        if self._alloc is not None:
+            bc.alloc = self._alloc.alloc
+            bc.free = self._alloc.free
+        self.storage = bc.storage
+        h = C.c_void_p()
+        with torch.cuda.device(device):
+            _check(L.lbm_create(self.mask.ctypes.data_as(C.POINTER(C.c_uint8)), self.nx, self.ny,
+                                float(tau), _dp(u), int(u.size), C.byref(bc), C.byref(h)))
+        self._h = h
+
+    # -- life cycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- stepping and forces
+    def step(self, n=1):
+        _check(lib().lbm_step(self._h, int(n)), self._h)
+
+    def force(self, scheme):
+        fx, fy = C.c_double(), C.c_double()
+        _check(lib().lbm_force(self._h, SCHEMES.get(scheme, scheme), C.byref(fx), C.byref(fy)),
+               self._h)
+        return fx.value, fy.value
+
+    def force_series(self, scheme, first=0, count=None):
+        if count is None:
+            count = self.steps_done - first
+        fx = np.zeros(max(count, 1))
+        fy = np.zeros(max(count, 1))
+        _check(lib().lbm_force_series(self._h, SCHEMES.get(scheme, scheme), int(first),
+                                      int(count), _dp(fx), _dp(fy)), self._h)
+        return fx[:count], fy[:count]
+
+    # -- state
+    def populations(self, out=None):
+        if out is None:
+            out = np.empty((9, self.ny, self.nx), np.float64)
+        _check(lib().lbm_populations(self._h, _dp(out)), self._h)
+        return out
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, np.float64).reshape(9, self.ny, self.nx)
+        _check(lib().lbm_set_populations(self._h, _dp(f)), self._h)
+
+    def links(self):
+        n = self.num_links
+        out = np.zeros(max(n, 1), np.int32)
+        cnt = C.c_long()
+        _check(lib().lbm_links(self._h, out.ctypes.data_as(C.POINTER(C.c_int32)), n,
+                               C.byref(cnt)), self._h)
+        return out[:cnt.value]
+
+    def control_volume(self):
+        cv = (C.c_int * 4)()
+        _check(lib().lbm_control_volume(self._h, cv), self._h)
+        return list(cv)
+
+    @property
+    def steps_done(self):
+        return lib().lbm_steps_done(self._h)
+
+    @property
+    def num_links(self):
+        return lib().lbm_num_links(self._h)
+
+    @property
+    def launch_count(self):
+        return lib().lbm_launch_count(self._h)
+
+    # -- measurement support
+    def set_kernel_timing(self, on):
+        _check(lib().lbm_set_kernel_timing(self._h, int(bool(on))), self._h)
+
+    def kernel_times(self, reset=False):
+        ms = (C.c_double * 2)()
+        n = (C.c_long * 2)()
+        _check(lib().lbm_kernel_times(self._h, ms, n, int(bool(reset))), self._h)
+        return {"collide_stream": (ms[0], n[0]), "link_force": (ms[1], n[1])}

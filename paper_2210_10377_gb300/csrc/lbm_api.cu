@@ -1,0 +1,786 @@
+// lbm_api.cu -- the C ABI declared in include/gblbm.h: argument checks, device
+// memory, set-up sequence, the step loop (CUDA graphs of whole step pairs) and
+// read-back.  All arithmetic of the method runs in the kernels of
+// lbm_setup.cu and lbm_step.cu.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace gblbm;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+constexpr int GRAPH_STEPS = 16;  // steps per captured graph (even: buffers return)
+constexpr int TIMING_BATCH = 64;
+
+}  // namespace
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, pitch = 0, periodic = 0, storage = 0;
+    double tau = 0, omega = 0, rho0 = 1, g[2] = {0, 0};
+    int cv[4] = {0, 0, 0, 0}, cvt[4] = {0, 0, 0, 0};
+    int tiles_x = 0, tiles_y = 0, n_cv_tiles = 0;
+    int record_series = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    lbm_alloc_fn alloc_fn = nullptr;
+    lbm_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    size_t elem = 4;
+    long long plane = 0;
+    void *pop[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t *mask_d = nullptr;
+    uint16_t *nbits = nullptr;
+    uint8_t *tile_flag = nullptr;
+    int32_t *links = nullptr;
+    long long nlinks = 0;
+    double *u_row = nullptr;
+    void *inlet = nullptr;
+    double *partials = nullptr;
+    double *series = nullptr;
+    long long series_cap = 0;
+    double *carry = nullptr;     // [8]
+    long long *step_ctr = nullptr;
+    int *status = nullptr;       // [2]
+    long long t = 0;
+    int precollision = 1;
+    long long carry_from = 0;    // first step of the current DRTT chain
+    long long drtt_ready = 0;    // DRTT(s) is final for s < drtt_ready
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur][big/small]
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    double kt_ms[2] = {0, 0};
+    long kt_n[2] = {0, 0};
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status set_err(lbm_ctx *h, lbm_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_thread_err = buf;
+    return code;
+}
+
+lbm_status cuda_err(lbm_ctx *h, cudaError_t e, const char *what)
+{
+    return set_err(h, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, expr, what)                               \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return cuda_err(h, e_, what); \
+    } while (0)
+
+void *dev_alloc(lbm_ctx *h, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (h->alloc_fn) return h->alloc_fn(bytes, (void *)h->stream, h->alloc_user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(lbm_ctx *h, void *p)
+{
+    if (!p) return;
+    if (h->free_fn)
+        h->free_fn(p, h->alloc_user);
+    else
+        cudaFree(p);
+}
+
+size_t storage_bytes(int storage)
+{
+    switch (storage) {
+    case LBM_F64: return 8;
+    case LBM_F16_DEV: return 2;
+    default: return 4;
+    }
+}
+
+// Default control volume; the same rule is stated in gblbm.h.
+void auto_cv(const uint8_t *mask, int nx, int ny, int periodic, int *cv)
+{
+    int xmin = nx, xmax = -1, ymin = ny, ymax = -1;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            if (mask[(size_t)y * nx + x]) {
+                xmin = x < xmin ? x : xmin;
+                xmax = x > xmax ? x : xmax;
+                ymin = y < ymin ? y : ymin;
+                ymax = y > ymax ? y : ymax;
+            }
+    if (xmax < 0) {
+        cv[0] = periodic ? 0 : 1;
+        cv[1] = periodic ? nx - 1 : nx - 2;
+        cv[2] = 0;
+        cv[3] = ny - 1;
+        return;
+    }
+    int m = (xmax - xmin + 1 + 3) / 4;
+    if (m < 4) m = 4;
+    int x0 = xmin - m, x1 = xmax + m, y0 = ymin - m, y1 = ymax + m;
+    if (periodic) {
+        if (x0 < 1 || x1 > nx - 2) {
+            x0 = 0;
+            x1 = nx - 1;
+        }
+    } else {
+        x0 = x0 < 1 ? 1 : x0;
+        x1 = x1 > nx - 2 ? nx - 2 : x1;
+    }
+    if (y0 < 1 || y1 > ny - 2) {
+        y0 = 0;
+        y1 = ny - 1;
+    }
+    cv[0] = x0;
+    cv[1] = x1;
+    cv[2] = y0;
+    cv[3] = y1;
+}
+
+bool range_ok(int lo, int hi, int n, bool whole_allowed)
+{
+    if (lo > hi) return false;
+    if (lo >= 1 && hi <= n - 2) return true;
+    return whole_allowed && lo == 0 && hi == n - 1;
+}
+
+StepArgs step_args(lbm_ctx *h, int src, int precollision)
+{
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = h->pop[src];
+    a.dst = h->pop[src ^ 1];
+    a.nbits = h->nbits;
+    a.tile_flag = h->tile_flag;
+    a.inlet = h->inlet;
+    a.partials = h->partials;
+    a.status = h->status;
+    a.step_ctr = h->step_ctr;
+    a.plane = h->plane;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.periodic = h->periodic;
+    a.precollision = precollision;
+    a.tiles_x = h->tiles_x;
+    a.omega = h->omega;
+    a.rho0 = h->rho0;
+    a.gx = h->g[0];
+    a.gy = h->g[1];
+    memcpy(a.cv, h->cv, sizeof(a.cv));
+    memcpy(a.cvt, h->cvt, sizeof(a.cvt));
+    return a;
+}
+
+LinkArgs link_args(lbm_ctx *h, int src, int precollision, int drtt_only)
+{
+    LinkArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = h->pop[src];
+    a.dst = h->pop[src ^ 1];
+    a.nbits = h->nbits;
+    a.links = h->links;
+    a.nlinks = h->nlinks;
+    a.partials = h->partials;
+    a.n_partials = h->n_cv_tiles;
+    a.series = h->series;
+    a.carry = h->carry;
+    a.step_ctr = h->step_ctr;
+    a.plane = h->plane;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.periodic = h->periodic;
+    a.precollision = precollision;
+    a.record_series = h->record_series;
+    a.drtt_only = drtt_only;
+    a.rho0 = h->rho0;
+    return a;
+}
+
+// One step t -> t+1 from buffer src: collide-stream, then the link kernel.
+cudaError_t launch_one_step(lbm_ctx *h, int src, int precollision, cudaEvent_t *ev)
+{
+    StepArgs sa = step_args(h, src, precollision);
+    if (ev) cudaEventRecord(ev[0], h->stream);
+    cudaError_t e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false, h->stream);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], h->stream);
+    LinkArgs la = link_args(h, src, precollision, 0);
+    e = launch_link_force(h->storage, la, h->stream);
+    if (ev) cudaEventRecord(ev[2], h->stream);
+    h->launches += 2;
+    return e;
+}
+
+void drop_graphs(lbm_ctx *h)
+{
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < 2; ++k)
+            if (h->graph[p][k]) {
+                cudaGraphExecDestroy(h->graph[p][k]);
+                h->graph[p][k] = nullptr;
+            }
+}
+
+lbm_status build_graph(lbm_ctx *h, int p, int k)
+{
+    int steps = k == 0 ? GRAPH_STEPS : 2;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t le = cudaSuccess;
+    long long saved = h->launches;
+    for (int s = 0; s < steps && le == cudaSuccess; ++s) le = launch_one_step(h, p ^ (s & 1), 0, nullptr);
+    h->launches = saved;
+    cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_err(h, le, "capture step kernels");
+    }
+    if (ee != cudaSuccess) return cuda_err(h, ee, "end capture");
+    cudaError_t ie = cudaGraphInstantiate(&h->graph[p][k], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_err(h, ie, "instantiate graph");
+    return LBM_OK;
+}
+
+lbm_status ensure_series(lbm_ctx *h, long long need)
+{
+    if (!h->record_series) need = 2;
+    if (need <= h->series_cap) return LBM_OK;
+    long long cap = h->series_cap ? h->series_cap : 1024;
+    while (cap < need) cap *= 2;
+    double *ns = (double *)dev_alloc(h, sizeof(double) * 8 * cap);
+    if (!ns) return set_err(h, LBM_ENOMEM, "force series: allocation of %lld steps failed", cap);
+    CK(h, cudaMemsetAsync(ns, 0, sizeof(double) * 8 * cap, h->stream), "memset series");
+    if (h->series)
+        CK(h, cudaMemcpyAsync(ns, h->series, sizeof(double) * 8 * h->series_cap,
+                              cudaMemcpyDeviceToDevice, h->stream),
+           "copy series");
+    CK(h, cudaStreamSynchronize(h->stream), "sync");
+    dev_free(h, h->series);
+    h->series = ns;
+    h->series_cap = cap;
+    drop_graphs(h);
+    return LBM_OK;
+}
+
+lbm_status flush_timing(lbm_ctx *h, int nev)
+{
+    if (nev == 0) return LBM_OK;
+    CK(h, cudaEventSynchronize(h->events[3 * (nev - 1) + 2]), "timing sync");
+    for (int k = 0; k < nev; ++k) {
+        float a = 0, b = 0;
+        CK(h, cudaEventElapsedTime(&a, h->events[3 * k], h->events[3 * k + 1]), "elapsed");
+        CK(h, cudaEventElapsedTime(&b, h->events[3 * k + 1], h->events[3 * k + 2]), "elapsed");
+        h->kt_ms[0] += a;
+        h->kt_ms[1] += b;
+        h->kt_n[0] += 1;
+        h->kt_n[1] += 1;
+    }
+    return LBM_OK;
+}
+
+// Complete DRTT(T-1) with a momentum-only pass over the control-volume tiles.
+lbm_status finalize_drtt(lbm_ctx *h)
+{
+    if (h->drtt_ready >= h->t) return LBM_OK;
+    if (h->t < 1 || h->t - 1 < h->carry_from || h->precollision)
+        return set_err(h, LBM_ESTATE, "DRTT of step %lld needs J of step %lld, which is not available",
+                       h->t - 1, h->t);
+    StepArgs sa = step_args(h, h->cur, 0);
+    sa.tile_off_x = h->cvt[0];
+    sa.tile_off_y = h->cvt[2];
+    CK(h, launch_collide_stream(h->storage, sa, h->cvt[1] - h->cvt[0] + 1, h->cvt[3] - h->cvt[2] + 1,
+                                true, h->stream),
+       "momentum pass");
+    LinkArgs la = link_args(h, h->cur, 0, 1);
+    CK(h, launch_link_force(h->storage, la, h->stream), "DRTT finalize");
+    h->launches += 2;
+    h->drtt_ready = h->t;
+    return LBM_OK;
+}
+
+void free_all(lbm_ctx *h)
+{
+    drop_graphs(h);
+    for (auto e : h->events) cudaEventDestroy(e);
+    h->events.clear();
+    void *bufs[] = {h->pop[0], h->pop[1], h->mask_d, h->nbits, h->tile_flag, h->links,
+                    h->u_row, h->inlet, h->partials, h->series, h->carry, h->step_ctr,
+                    h->status};
+    for (void *p : bufs) dev_free(h, p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+bool finite_all(const double *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_bc_default(lbm_bc *bc)
+{
+    if (!bc) return;
+    memset(bc, 0, sizeof(*bc));
+    bc->kind = LBM_BC_CHANNEL;
+    bc->storage = LBM_F32;
+    bc->rho0 = 1.0;
+    bc->cv[0] = -1;
+    bc->record_series = 1;
+}
+
+lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const double *u_in,
+                      int n_u_in, const lbm_bc *bc_in, lbm_ctx **out)
+{
+    if (!out) return set_err(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_bc bc;
+    if (bc_in)
+        bc = *bc_in;
+    else
+        lbm_bc_default(&bc);
+    if (!mask || !u_in) return set_err(nullptr, LBM_EINVAL, "mask and u_in must not be NULL");
+    if (nx < 4 || ny < 3) return set_err(nullptr, LBM_EINVAL, "grid %dx%d too small (nx >= 4, ny >= 3)", nx, ny);
+    if ((long long)nx * ny * 8 >= (1LL << 31))
+        return set_err(nullptr, LBM_EINVAL, "grid %dx%d too large for int32 link indices", nx, ny);
+    if (!(tau > 0.5) || !std::isfinite(tau))
+        return set_err(nullptr, LBM_EINVAL, "tau must be finite and > 0.5 (got %g)", tau);
+    if (n_u_in != 1 && n_u_in != ny)
+        return set_err(nullptr, LBM_EINVAL, "n_u_in must be 1 or ny (got %d)", n_u_in);
+    if (!finite_all(u_in, n_u_in)) return set_err(nullptr, LBM_EINVAL, "u_in is not finite");
+    if (bc.kind != LBM_BC_CHANNEL && bc.kind != LBM_BC_PERIODIC)
+        return set_err(nullptr, LBM_EINVAL, "unknown boundary kind %d", bc.kind);
+    if (bc.storage < LBM_F64 || bc.storage > LBM_F16_DEV)
+        return set_err(nullptr, LBM_EINVAL, "unknown storage %d", bc.storage);
+    if (!(bc.rho0 > 0) || !std::isfinite(bc.rho0))
+        return set_err(nullptr, LBM_EINVAL, "rho0 must be finite and > 0");
+    if (!finite_all(bc.body_force, 2)) return set_err(nullptr, LBM_EINVAL, "body force is not finite");
+    if ((bc.alloc == nullptr) != (bc.free == nullptr))
+        return set_err(nullptr, LBM_EINVAL, "alloc and free must be given together");
+    const int periodic = bc.kind == LBM_BC_PERIODIC;
+    if (!periodic) {
+        const int cols[4] = {0, 1, nx - 2, nx - 1};
+        for (int y = 0; y < ny; ++y)
+            for (int c : cols)
+                if (mask[(size_t)y * nx + c])
+                    return set_err(nullptr, LBM_EINVAL,
+                                   "solid node at (%d, %d): columns 0, 1, nx-2, nx-1 of a channel must be fluid",
+                                   c, y);
+    }
+    int cv[4];
+    if (bc.cv[0] < 0) {
+        auto_cv(mask, nx, ny, periodic, cv);
+    } else {
+        memcpy(cv, bc.cv, sizeof(cv));
+        if (!range_ok(cv[0], cv[1], nx, periodic != 0) || !range_ok(cv[2], cv[3], ny, true))
+            return set_err(nullptr, LBM_EINVAL,
+                           "control volume {%d,%d,%d,%d} must lie within [1, n-2] (or span a periodic direction)",
+                           cv[0], cv[1], cv[2], cv[3]);
+    }
+    int ndev = 0;
+    cudaError_t de = cudaGetDeviceCount(&ndev);
+    if (de != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_err(nullptr, LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(de));
+    }
+
+    lbm_ctx *h = new (std::nothrow) lbm_ctx;
+    if (!h) return set_err(nullptr, LBM_ENOMEM, "host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->periodic = periodic;
+    h->storage = bc.storage;
+    h->tau = tau;
+    h->omega = 1.0 / tau;
+    h->rho0 = bc.rho0;
+    h->g[0] = bc.body_force[0];
+    h->g[1] = bc.body_force[1];
+    memcpy(h->cv, cv, sizeof(cv));
+    h->record_series = bc.record_series ? 1 : 0;
+    h->alloc_fn = bc.alloc;
+    h->free_fn = bc.free;
+    h->alloc_user = bc.alloc_user;
+    h->elem = storage_bytes(bc.storage);
+    h->pitch = (nx + PITCH_ALIGN - 1) / PITCH_ALIGN * PITCH_ALIGN;
+    h->plane = (long long)ny * h->pitch;
+    h->tiles_x = (nx + TILE_X - 1) / TILE_X;
+    h->tiles_y = (ny + TILE_ROWS - 1) / TILE_ROWS;
+    {
+        int hx0 = cv[0] - 1 < 0 ? 0 : cv[0] - 1, hx1 = cv[1] + 1 > nx - 1 ? nx - 1 : cv[1] + 1;
+        int hy0 = cv[2] - 1 < 0 ? 0 : cv[2] - 1, hy1 = cv[3] + 1 > ny - 1 ? ny - 1 : cv[3] + 1;
+        h->cvt[0] = hx0 / TILE_X;
+        h->cvt[1] = hx1 / TILE_X;
+        h->cvt[2] = hy0 / TILE_ROWS;
+        h->cvt[3] = hy1 / TILE_ROWS;
+        h->n_cv_tiles = (h->cvt[1] - h->cvt[0] + 1) * (h->cvt[3] - h->cvt[2] + 1);
+    }
+    if (bc.cuda_stream) {
+        h->stream = (cudaStream_t)bc.cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_err(nullptr, e, "stream create");
+        }
+        h->own_stream = true;
+    }
+
+    lbm_status st = LBM_OK;
+    auto fail = [&](lbm_status s) {
+        g_thread_err = h->err;
+        free_all(h);
+        delete h;
+        return s;
+    };
+#define CKC(expr, what)                                  \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return fail(cuda_err(h, e_, what)); \
+    } while (0)
+#define ALLOC(ptr, type, bytes)                                                       \
+    do {                                                                              \
+        ptr = (type)dev_alloc(h, (bytes));                                            \
+        if (!ptr) return fail(set_err(h, LBM_ENOMEM, "device allocation of %zu bytes failed", (size_t)(bytes))); \
+    } while (0)
+
+    const size_t N = (size_t)nx * ny;
+    const size_t pop_bytes = 9 * (size_t)h->plane * h->elem;
+    ALLOC(h->pop[0], void *, pop_bytes);
+    ALLOC(h->pop[1], void *, pop_bytes);
+    ALLOC(h->mask_d, uint8_t *, N);
+    ALLOC(h->nbits, uint16_t *, sizeof(uint16_t) * h->plane);
+    ALLOC(h->tile_flag, uint8_t *, (size_t)h->tiles_x * h->tiles_y);
+    ALLOC(h->u_row, double *, sizeof(double) * ny);
+    ALLOC(h->inlet, void *, 9 * (size_t)ny * h->elem);
+    ALLOC(h->partials, double *, sizeof(double) * 4 * h->n_cv_tiles);
+    ALLOC(h->carry, double *, sizeof(double) * 8);
+    ALLOC(h->step_ctr, long long *, sizeof(long long));
+    ALLOC(h->status, int *, sizeof(int) * 2);
+    st = ensure_series(h, 1024);
+    if (st != LBM_OK) return fail(st);
+
+    std::vector<double> urow(ny);
+    for (int y = 0; y < ny; ++y) urow[y] = n_u_in == 1 ? u_in[0] : u_in[y];
+    cudaStream_t s = h->stream;
+    CKC(cudaMemsetAsync(h->pop[0], 0, pop_bytes, s), "memset");
+    CKC(cudaMemsetAsync(h->pop[1], 0, pop_bytes, s), "memset");
+    CKC(cudaMemsetAsync(h->nbits, 0, sizeof(uint16_t) * h->plane, s), "memset");
+    CKC(cudaMemsetAsync(h->partials, 0, sizeof(double) * 4 * h->n_cv_tiles, s), "memset");
+    CKC(cudaMemsetAsync(h->carry, 0, sizeof(double) * 8, s), "memset");
+    CKC(cudaMemsetAsync(h->step_ctr, 0, sizeof(long long), s), "memset");
+    const int status0[2] = {0, INT_MAX};
+    CKC(cudaMemcpyAsync(h->status, status0, sizeof(status0), cudaMemcpyHostToDevice, s), "H2D status");
+    CKC(cudaMemcpyAsync(h->mask_d, mask, N, cudaMemcpyHostToDevice, s), "H2D mask");
+    CKC(cudaMemcpyAsync(h->u_row, urow.data(), sizeof(double) * ny, cudaMemcpyHostToDevice, s), "H2D u_in");
+    CKC(launch_node_bits(h->mask_d, h->nbits, nx, ny, h->pitch, periodic, s), "node bits");
+    CKC(launch_tile_flags(h->nbits, nx, ny, h->pitch, periodic, h->tile_flag, h->tiles_x, h->tiles_y, s),
+        "tile flags");
+    // link list: count, scan, scatter
+    const int nb = link_blocks(nx, ny);
+    int *blk = nullptr;
+    long long *total_d = nullptr;
+    ALLOC(blk, int *, sizeof(int) * nb);
+    total_d = (long long *)dev_alloc(h, sizeof(long long));
+    if (!total_d) {
+        dev_free(h, blk);
+        return fail(set_err(h, LBM_ENOMEM, "device allocation failed"));
+    }
+    cudaError_t le = launch_link_count(h->nbits, nx, ny, h->pitch, blk, nb, s);
+    if (le == cudaSuccess) le = launch_scan_blocks(blk, nb, total_d, s);
+    long long total = 0;
+    if (le == cudaSuccess) le = cudaMemcpyAsync(&total, total_d, sizeof(total), cudaMemcpyDeviceToHost, s);
+    if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+    if (le == cudaSuccess) {
+        h->nlinks = total;
+        h->links = (int32_t *)dev_alloc(h, sizeof(int32_t) * (total > 0 ? total : 1));
+        if (!h->links) {
+            dev_free(h, blk);
+            dev_free(h, total_d);
+            return fail(set_err(h, LBM_ENOMEM, "device allocation of the link list failed"));
+        }
+        le = launch_link_scatter(h->nbits, nx, ny, h->pitch, blk, h->links, total, s);
+    }
+    if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+    dev_free(h, blk);
+    dev_free(h, total_d);
+    if (le != cudaSuccess) return fail(cuda_err(h, le, "link list"));
+    CKC(launch_init(h->storage, h->pop[0], h->plane, h->mask_d, nx, ny, h->pitch, h->u_row, h->rho0,
+                    h->inlet, s),
+        "initial state");
+    CKC(cudaStreamSynchronize(s), "sync");
+    h->launches = 6;
+#undef CKC
+#undef ALLOC
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *h, int n)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (n < 0) return set_err(h, LBM_EINVAL, "n must be >= 0");
+    if (n == 0) return LBM_OK;
+    lbm_status st = ensure_series(h, h->t + n);
+    if (st != LBM_OK) return st;
+    const int status0[2] = {0, INT_MAX};
+    CK(h, cudaMemcpyAsync(h->status, status0, sizeof(status0), cudaMemcpyHostToDevice, h->stream),
+       "H2D status");
+    if (h->timing && (int)h->events.size() < 3 * TIMING_BATCH) {
+        h->events.resize(3 * TIMING_BATCH, nullptr);
+        for (auto &e : h->events)
+            if (!e) CK(h, cudaEventCreate(&e), "event create");
+    }
+    int nev = 0;
+    while (n > 0) {
+        if (h->precollision || h->timing || n < 2) {
+            cudaEvent_t *ev = h->timing ? &h->events[3 * nev] : nullptr;
+            CK(h, launch_one_step(h, h->cur, h->precollision, ev), "step launch");
+            if (h->timing && ++nev == TIMING_BATCH) {
+                st = flush_timing(h, nev);
+                if (st != LBM_OK) return st;
+                nev = 0;
+            }
+            h->cur ^= 1;
+            h->precollision = 0;
+            h->t += 1;
+            n -= 1;
+        } else {
+            int k = n >= GRAPH_STEPS ? 0 : 1;
+            int steps = k == 0 ? GRAPH_STEPS : 2;
+            if (!h->graph[h->cur][k]) {
+                st = build_graph(h, h->cur, k);
+                if (st != LBM_OK) return st;
+            }
+            CK(h, cudaGraphLaunch(h->graph[h->cur][k], h->stream), "graph launch");
+            h->launches += 2 * steps;
+            h->t += steps;
+            n -= steps;
+        }
+    }
+    if (h->timing) {
+        st = flush_timing(h, nev);
+        if (st != LBM_OK) return st;
+    }
+    int status[2];
+    CK(h, cudaMemcpyAsync(status, h->status, sizeof(status), cudaMemcpyDeviceToHost, h->stream),
+       "D2H status");
+    CK(h, cudaStreamSynchronize(h->stream), "step sync");
+    if (h->t - 1 > h->carry_from) h->drtt_ready = h->t - 1 > h->drtt_ready ? h->t - 1 : h->drtt_ready;
+    if (status[0]) return set_err(h, LBM_EUNSTABLE, "rho <= 0 or NaN first seen at step %d", status[1]);
+    return LBM_OK;
+}
+
+lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, double *fx, double *fy)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (scheme < 0 || scheme > 3) return set_err(h, LBM_EINVAL, "unknown scheme %d", scheme);
+    if (count < 0 || first < 0 || first + count > h->t)
+        return set_err(h, LBM_EINVAL, "steps [%ld, %ld) outside [0, %lld)", first, first + count, h->t);
+    if (count == 0) return LBM_OK;
+    if (!fx || !fy) return set_err(h, LBM_EINVAL, "fx and fy must not be NULL");
+    if (!h->record_series && first < h->t - 2)
+        return set_err(h, LBM_EINVAL, "only the last two steps are kept (record_series = 0)");
+    if (scheme == LBM_FORCE_DRTT && first + count > h->drtt_ready) {
+        lbm_status st = finalize_drtt(h);
+        if (st != LBM_OK) return st;
+    }
+    std::vector<double> rows((size_t)count * 8);
+    if (h->record_series) {
+        CK(h, cudaMemcpyAsync(rows.data(), h->series + 8 * first, sizeof(double) * 8 * count,
+                              cudaMemcpyDeviceToHost, h->stream),
+           "D2H series");
+    } else {
+        for (long k = 0; k < count; ++k)
+            CK(h, cudaMemcpyAsync(rows.data() + 8 * k, h->series + 8 * ((first + k) & 1),
+                                  sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream),
+               "D2H series");
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "sync");
+    const int col = scheme == LBM_FORCE_MEA_A ? 0 : scheme == LBM_FORCE_MEA_B ? 2 : scheme == LBM_FORCE_DRTT ? 4 : 6;
+    for (long k = 0; k < count; ++k) {
+        fx[k] = rows[8 * k + col];
+        fy[k] = rows[8 * k + col + 1];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_force(lbm_ctx *h, int scheme, double *fx, double *fy)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (h->t < 1) return set_err(h, LBM_ESTATE, "no step has been taken");
+    return lbm_force_series(h, scheme, (long)(h->t - 1), 1, fx, fy);
+}
+
+lbm_status lbm_populations(lbm_ctx *h, double *out)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (!out) return set_err(h, LBM_EINVAL, "out must not be NULL");
+    const size_t N = (size_t)h->nx * h->ny;
+    double *scratch = (double *)dev_alloc(h, sizeof(double) * N);
+    if (!scratch) return set_err(h, LBM_ENOMEM, "scratch allocation failed");
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < 9 && st == LBM_OK; ++i) {
+        cudaError_t e = launch_gather(h->storage, h->pop[h->cur], h->nbits, h->inlet, h->plane, h->nx,
+                                      h->ny, h->pitch, h->periodic, h->precollision, h->rho0, i,
+                                      scratch, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out + i * N, scratch, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_err(h, e, "gather populations");
+        h->launches += 1;
+    }
+    dev_free(h, scratch);
+    return st;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *h, const double *in)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (!in) return set_err(h, LBM_EINVAL, "in must not be NULL");
+    const size_t N = (size_t)h->nx * h->ny;
+    for (size_t k = 0; k < 9 * N; ++k)
+        if (!std::isfinite(in[k])) return set_err(h, LBM_EINVAL, "populations must be finite");
+    if (h->t >= 1 && h->drtt_ready < h->t && !h->precollision && h->t - 1 >= h->carry_from) {
+        lbm_status st = finalize_drtt(h);
+        if (st != LBM_OK) return st;
+    }
+    double *scratch = (double *)dev_alloc(h, sizeof(double) * N);
+    if (!scratch) return set_err(h, LBM_ENOMEM, "scratch allocation failed");
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < 9 && st == LBM_OK; ++i) {
+        cudaError_t e = cudaMemcpyAsync(scratch, in + i * N, sizeof(double) * N, cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e == cudaSuccess)
+            e = launch_scatter_pop(h->storage, h->pop[h->cur], h->nbits, h->plane, h->nx, h->ny,
+                                   h->pitch, h->rho0, i, scratch, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_err(h, e, "set populations");
+        h->launches += 1;
+    }
+    dev_free(h, scratch);
+    if (st != LBM_OK) return st;
+    CK(h, cudaMemsetAsync(h->carry, 0, sizeof(double) * 8, h->stream), "memset carry");
+    CK(h, cudaStreamSynchronize(h->stream), "sync");
+    h->precollision = 1;
+    h->carry_from = h->t;
+    if (h->drtt_ready < h->t) h->drtt_ready = h->t;
+    return LBM_OK;
+}
+
+lbm_status lbm_links(lbm_ctx *h, int32_t *out, long cap, long *count)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (count) *count = (long)h->nlinks;
+    long n = cap < (long)h->nlinks ? cap : (long)h->nlinks;
+    if (n > 0) {
+        if (!out) return set_err(h, LBM_EINVAL, "out must not be NULL");
+        CK(h, cudaMemcpyAsync(out, h->links, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream),
+           "D2H links");
+        CK(h, cudaStreamSynchronize(h->stream), "sync");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_control_volume(lbm_ctx *h, int *cv)
+{
+    if (!h || !cv) return set_err(h, LBM_EINVAL, "NULL argument");
+    memcpy(cv, h->cv, sizeof(h->cv));
+    return LBM_OK;
+}
+
+lbm_status lbm_naca_mask(int nx, int ny, double chord, double thickness, double alpha_deg,
+                         double xc, double yc, int closed_te, uint8_t *out)
+{
+    if (nx <= 0 || ny <= 0 || !(chord > 0) || !(thickness > 0) || !out || !std::isfinite(alpha_deg) ||
+        !std::isfinite(xc) || !std::isfinite(yc))
+        return set_err(nullptr, LBM_EINVAL, "bad NACA section arguments");
+    double a = alpha_deg * M_PI / 180.0;
+    double ca = cos(a), sa = sin(a);
+    size_t N = (size_t)nx * ny;
+    uint8_t *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, N);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_err(nullptr, e, "cudaMalloc mask");
+    }
+    e = launch_naca_mask(d, nx, ny, chord, thickness, ca, sa, xc, yc, closed_te, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, N, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_err(nullptr, e, "NACA mask");
+    return LBM_OK;
+}
+
+long lbm_steps_done(const lbm_ctx *h) { return h ? (long)h->t : -1; }
+
+long lbm_num_links(const lbm_ctx *h) { return h ? (long)h->nlinks : -1; }
+
+lbm_status lbm_set_kernel_timing(lbm_ctx *h, int on)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    h->timing = on != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_kernel_times(lbm_ctx *h, double *ms, long *launches, int reset)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    for (int k = 0; k < 2; ++k) {
+        if (ms) ms[k] = h->kt_ms[k];
+        if (launches) launches[k] = h->kt_n[k];
+    }
+    if (reset) {
+        h->kt_ms[0] = h->kt_ms[1] = 0;
+        h->kt_n[0] = h->kt_n[1] = 0;
+    }
+    return LBM_OK;
+}
+
+long lbm_launch_count(const lbm_ctx *h) { return h ? (long)h->launches : -1; }
+
+const char *lbm_last_error(const lbm_ctx *h)
+{
+    return h ? h->err.c_str() : g_thread_err.c_str();
+}
+
+void lbm_destroy(lbm_ctx *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

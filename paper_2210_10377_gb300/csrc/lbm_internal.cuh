@@ -1,0 +1,151 @@
+// lbm_internal.cuh -- declarations shared by the library's translation units.
+//
+// Layout in HBM (all device buffers owned by the handle):
+//   populations  two buffers, each 9 planes [ny][pitch] of the storage type
+//                (pitch = nx rounded up to 64 elements, so every row starts on a
+//                128-byte boundary for FP16 and wider types);
+//   nbits        uint16 [ny][pitch]: bit 0 = node is solid, bit i (1..8) =
+//                neighbour n + c_i is solid (y periodic, x periodic only for a
+//                fully periodic domain);
+//   tile_flag    uint8 per collide-stream tile: nonzero when a solid node lies in
+//                the tile or its one-node halo (those tiles take the checked
+//                bounce-back path);
+//   links        int32 [L], n*8 + (i-1), ascending;
+//   inlet        [9][ny] storage-type inlet populations feq(rho0, u_in(y));
+//   partials     double [n_cv_tiles][4] per-tile J(t) and gained-lost(t);
+//   series       double [steps][4 schemes][2] forces;
+//   carry        double [8]: J(t-1), GL(t-1), flag, spare;  step counter int64.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gblbm.h"
+
+namespace gblbm {
+
+// Collide-stream tile: 128 nodes along x by TILE_ROWS rows; one CTA of
+// 128 x 2 threads, each thread walks TILE_ROWS/2 rows of one column.
+constexpr int TILE_X = 128;
+constexpr int TILE_ROWS = 4;
+constexpr int ROWS_PER_THREAD = TILE_ROWS / 2;
+constexpr int PITCH_ALIGN = 64;
+constexpr int LINK_THREADS = 1024;
+
+// ---- D2Q9 (Section II, Table tabD2Q9) as compile-time functions ----
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+template <typename T>
+__host__ __device__ constexpr T wgt(int i) {
+    return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+
+// ---- storage traits ----
+template <int S> struct Traits;
+template <> struct Traits<LBM_F64> {
+    using store_t = double;
+    using comp_t = double;
+    static constexpr bool dev = false;
+};
+template <> struct Traits<LBM_F32> {
+    using store_t = float;
+    using comp_t = float;
+    static constexpr bool dev = false;
+};
+template <> struct Traits<LBM_F32_DEV> {
+    using store_t = float;
+    using comp_t = float;
+    static constexpr bool dev = true;
+};
+template <> struct Traits<LBM_F16_DEV> {
+    using store_t = __half;
+    using comp_t = float;
+    static constexpr bool dev = true;
+};
+
+__device__ __forceinline__ float to_comp(float v) { return v; }
+__device__ __forceinline__ double to_comp(double v) { return v; }
+__device__ __forceinline__ float to_comp(__half v) { return __half2float(v); }
+template <typename ST> __device__ __forceinline__ ST to_store(float v);
+template <> __device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+template <typename ST> __device__ __forceinline__ ST to_store(double v);
+template <> __device__ __forceinline__ double to_store<double>(double v) { return v; }
+
+// ---- kernel arguments ----
+struct StepArgs {
+    const void *src;         // populations at t-1 (post-collision) or t (pre-collision)
+    void *dst;               // post-collision populations at t
+    const uint16_t *nbits;
+    const uint8_t *tile_flag;
+    const void *inlet;       // [9][ny]
+    double *partials;        // [n_cv_tiles][4]
+    int *status;             // [0] flags, [1] first bad step
+    const long long *step_ctr;
+    long long plane;         // elements per plane = ny * pitch
+    int nx, ny, pitch;
+    int periodic;
+    int precollision;        // src holds f(t) (no pull this step)
+    int tiles_x;             // tiles per row band
+    int tile_off_x, tile_off_y;  // added to blockIdx (momentum-only pass)
+    double omega, rho0, gx, gy;
+    int cv[4];               // inclusive control-volume box
+    int cvt[4];              // inclusive tile rectangle holding the box and its halo
+};
+
+struct LinkArgs {
+    const void *src, *dst;
+    const uint16_t *nbits;
+    const int32_t *links;
+    long long nlinks;
+    const double *partials;
+    int n_partials;
+    double *series;
+    double *carry;           // J(t-1)[2], GL(t-1)[2], have_prev
+    long long *step_ctr;
+    long long plane;
+    int nx, ny, pitch, periodic, precollision;
+    int record_series;
+    int drtt_only;           // finalise DRTT(T-1) from a momentum-only pass
+    double rho0;
+};
+
+// ---- launchers (defined in the .cu files) ----
+cudaError_t launch_naca_mask(uint8_t *mask, int nx, int ny, double chord, double thickness,
+                             double ca, double sa, double xc, double yc, int closed_te,
+                             cudaStream_t st);
+cudaError_t launch_node_bits(const uint8_t *mask, uint16_t *nbits, int nx, int ny, int pitch,
+                             int periodic, cudaStream_t st);
+cudaError_t launch_link_count(const uint16_t *nbits, int nx, int ny, int pitch, int *block_cnt,
+                              int nblocks, cudaStream_t st);
+cudaError_t launch_scan_blocks(int *block_cnt, int nblocks, long long *total, cudaStream_t st);
+cudaError_t launch_link_scatter(const uint16_t *nbits, int nx, int ny, int pitch,
+                                const int *block_off, int32_t *links, long long cap,
+                                cudaStream_t st);
+cudaError_t launch_tile_flags(const uint16_t *nbits, int nx, int ny, int pitch, int periodic,
+                              uint8_t *flags, int tiles_x, int tiles_y, cudaStream_t st);
+int link_blocks(int nx, int ny);
+
+cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *mask, int nx,
+                        int ny, int pitch, const double *u_row, double rho0, void *inlet,
+                        cudaStream_t st);
+cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
+                                  bool momentum_only, cudaStream_t st);
+cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st);
+cudaError_t launch_gather(int storage, const void *pop, const uint16_t *nbits, const void *inlet,
+                          long long plane, int nx, int ny, int pitch, int periodic,
+                          int precollision, double rho0, int plane_i, double *out,
+                          cudaStream_t st);
+cudaError_t launch_scatter_pop(int storage, void *pop, const uint16_t *nbits, long long plane,
+                               int nx, int ny, int pitch, double rho0, int plane_i,
+                               const double *in, cudaStream_t st);
+
+}  // namespace gblbm
