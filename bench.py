@@ -39,6 +39,10 @@ def args_():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--profile", action="store_true",
+                   help="only create the solver and run warm-up + K steps (for ncu captures)")
+    p.add_argument("--workload", default=None, help="workload name (profile mode)")
+    p.add_argument("--storage", default=None, help="f64|f32|f32dev|f16dev (profile mode)")
     return p.parse_args()
 
 
@@ -334,8 +338,29 @@ def run_ours(a):
     return 0
 
 
+def run_profile(a):
+    """Warm-up + K steps of one workload and nothing else (the command that the
+    committed ncu summaries were taken on)."""
+    import torch
+
+    from paper_2210_10377_gb300 import binding, inputs
+    w = inputs.WORKLOADS[a.workload] if a.workload else inputs.LARGE_F32
+    storage = a.storage or w.storage
+    torch.cuda.set_device(0)
+    lat = binding.Lattice(naca_mask_device(w), w.tau, w.u_in, storage=storage)
+    lat.step(a.warmup)
+    ms = time_steps(torch, lat, a.steps)
+    print(json.dumps({"workload": w.name, "storage": storage, "steps": a.steps,
+                      "MLUPS": round(w.nodes * a.steps / (ms / 1e3) / 1e6, 1),
+                      "force_B": lat.force("B")}), flush=True)
+    lat.close()
+    return 0
+
+
 def main():
     a = args_()
+    if a.profile:
+        return run_profile(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

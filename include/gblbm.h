@@ -72,11 +72,19 @@ typedef enum {
     LBM_FORCE_MEA_B = 1,
     /* Discrete Reynolds transport theorem, Eq. (rtt7) (second form) and the
      * Appendix: F(t) = J(t) - J(t+1) + gained(t) - lost(t) over the control
-     * volume box.  Needs J(t+1), i.e. one step beyond t. */
+     * volume box, gained/lost = post-collision populations streaming into /
+     * out of the box between fluid nodes.  J(t) is summed on the stored
+     * post-collision state less the body-force momentum (equal to the
+     * pre-collision J(t) in exact arithmetic), J(t+1) on the pre-collision
+     * state.  Needs J(t+1), i.e. one step beyond t. */
     LBM_FORCE_DRTT = 2,
     /* Eq. (rtt4) read literally for algorithm A: lost momentum with f_i(x_f, t),
      * gained momentum with the bounced ft_i(x_f, t). Diagnostic. */
-    LBM_FORCE_MEA_A_RTT = 3
+    LBM_FORCE_MEA_A_RTT = 3,
+    /* Diagnostic, not a force: momentum the collision fails to conserve inside
+     * the control volume in the storage arithmetic, sum over its fluid nodes of
+     * c.(f - ft) + g; zero in exact arithmetic (BGK conserves momentum). */
+    LBM_DIAG_MOMENTUM_DEFECT = 4
 } lbm_scheme;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -93,7 +101,8 @@ typedef struct {
     int cv[4];            /* DRTT control volume, inclusive {x0, x1, y0, y1};
                              cv[0] < 0 selects the default box (see lbm_create) */
     int record_series;    /* 1: keep forces of every step; 0: only the last two */
-    void *cuda_stream;    /* cudaStream_t for all work of the handle; NULL = legacy default */
+    void *cuda_stream;    /* cudaStream_t for all work of the handle; NULL: the handle
+                             creates its own non-blocking stream */
     lbm_alloc_fn alloc;   /* NULL: cudaMalloc / cudaFree */
     lbm_free_fn free;
     void *alloc_user;
@@ -135,7 +144,7 @@ lbm_status lbm_step(lbm_ctx *h, int n);
  * (the transition T-1 -> T) for one lbm_scheme.  ESTATE before the first step. */
 lbm_status lbm_force(lbm_ctx *h, int scheme, double *fx, double *fy);
 
-/* Forces of steps [first, first+count) for one scheme into fx[count], fy[count].
+/* Forces of steps [first, first+count) for one lbm_scheme into fx[count], fy[count].
  * EINVAL if the range is not kept (record_series = 0 keeps the last two). */
 lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, double *fx,
                             double *fy);

@@ -16,8 +16,8 @@ from . import build as _build
 CHANNEL, PERIODIC = 0, 1
 F64, F32, F32_DEV, F16_DEV = 0, 1, 2, 3
 STORAGE = {"f64": F64, "f32": F32, "f32dev": F32_DEV, "f16dev": F16_DEV}
-MEA_A, MEA_B, DRTT, MEA_A_RTT = 0, 1, 2, 3
-SCHEMES = {"A": MEA_A, "B": MEA_B, "DRTT": DRTT, "A_RTT": MEA_A_RTT}
+MEA_A, MEA_B, DRTT, MEA_A_RTT, MOMENTUM_DEFECT = 0, 1, 2, 3, 4
+SCHEMES = {"A": MEA_A, "B": MEA_B, "DRTT": DRTT, "A_RTT": MEA_A_RTT, "DEFECT": MOMENTUM_DEFECT}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT",
           6: "ESTATE"}
 HEADER = os.path.join(_build.ROOT, "include", "gblbm.h")

@@ -46,6 +46,9 @@ struct lbm_ctx {
     double *u_row = nullptr;
     void *inlet = nullptr;
     double *partials = nullptr;
+    double *link_partials = nullptr;
+    unsigned int *ticket = nullptr;
+    int link_ctas = 1;
     double *series = nullptr;
     long long series_cap = 0;
     double *carry = nullptr;     // [8]
@@ -209,6 +212,9 @@ LinkArgs link_args(lbm_ctx *h, int src, int precollision, int drtt_only)
     a.nlinks = h->nlinks;
     a.partials = h->partials;
     a.n_partials = h->n_cv_tiles;
+    a.link_partials = h->link_partials;
+    a.ticket = h->ticket;
+    a.n_ctas = h->link_ctas;
     a.series = h->series;
     a.carry = h->carry;
     a.step_ctr = h->step_ctr;
@@ -276,11 +282,11 @@ lbm_status ensure_series(lbm_ctx *h, long long need)
     if (need <= h->series_cap) return LBM_OK;
     long long cap = h->series_cap ? h->series_cap : 1024;
     while (cap < need) cap *= 2;
-    double *ns = (double *)dev_alloc(h, sizeof(double) * 8 * cap);
+    double *ns = (double *)dev_alloc(h, sizeof(double) * SERIES_ROW * cap);
     if (!ns) return set_err(h, LBM_ENOMEM, "force series: allocation of %lld steps failed", cap);
-    CK(h, cudaMemsetAsync(ns, 0, sizeof(double) * 8 * cap, h->stream), "memset series");
+    CK(h, cudaMemsetAsync(ns, 0, sizeof(double) * SERIES_ROW * cap, h->stream), "memset series");
     if (h->series)
-        CK(h, cudaMemcpyAsync(ns, h->series, sizeof(double) * 8 * h->series_cap,
+        CK(h, cudaMemcpyAsync(ns, h->series, sizeof(double) * SERIES_ROW * h->series_cap,
                               cudaMemcpyDeviceToDevice, h->stream),
            "copy series");
     CK(h, cudaStreamSynchronize(h->stream), "sync");
@@ -333,8 +339,8 @@ void free_all(lbm_ctx *h)
     for (auto e : h->events) cudaEventDestroy(e);
     h->events.clear();
     void *bufs[] = {h->pop[0], h->pop[1], h->mask_d, h->nbits, h->tile_flag, h->links,
-                    h->u_row, h->inlet, h->partials, h->series, h->carry, h->step_ctr,
-                    h->status};
+                    h->u_row, h->inlet, h->partials, h->link_partials, h->ticket, h->series,
+                    h->carry, h->step_ctr, h->status};
     for (void *p : bufs) dev_free(h, p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -484,7 +490,9 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     ALLOC(h->tile_flag, uint8_t *, (size_t)h->tiles_x * h->tiles_y);
     ALLOC(h->u_row, double *, sizeof(double) * ny);
     ALLOC(h->inlet, void *, 9 * (size_t)ny * h->elem);
-    ALLOC(h->partials, double *, sizeof(double) * 4 * h->n_cv_tiles);
+    ALLOC(h->partials, double *, sizeof(double) * CV_PARTIAL * h->n_cv_tiles);
+    ALLOC(h->link_partials, double *, sizeof(double) * LINK_PARTIAL * MAX_LINK_CTAS);
+    ALLOC(h->ticket, unsigned int *, sizeof(unsigned int));
     ALLOC(h->carry, double *, sizeof(double) * 8);
     ALLOC(h->step_ctr, long long *, sizeof(long long));
     ALLOC(h->status, int *, sizeof(int) * 2);
@@ -497,7 +505,8 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     CKC(cudaMemsetAsync(h->pop[0], 0, pop_bytes, s), "memset");
     CKC(cudaMemsetAsync(h->pop[1], 0, pop_bytes, s), "memset");
     CKC(cudaMemsetAsync(h->nbits, 0, sizeof(uint16_t) * h->plane, s), "memset");
-    CKC(cudaMemsetAsync(h->partials, 0, sizeof(double) * 4 * h->n_cv_tiles, s), "memset");
+    CKC(cudaMemsetAsync(h->partials, 0, sizeof(double) * CV_PARTIAL * h->n_cv_tiles, s), "memset");
+    CKC(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s), "memset");
     CKC(cudaMemsetAsync(h->carry, 0, sizeof(double) * 8, s), "memset");
     CKC(cudaMemsetAsync(h->step_ctr, 0, sizeof(long long), s), "memset");
     const int status0[2] = {0, INT_MAX};
@@ -524,6 +533,11 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if (le == cudaSuccess) le = cudaStreamSynchronize(s);
     if (le == cudaSuccess) {
         h->nlinks = total;
+        {
+            long long work = total > h->n_cv_tiles ? total : h->n_cv_tiles;
+            long long c = (work + LINK_THREADS - 1) / LINK_THREADS;
+            h->link_ctas = (int)(c < 1 ? 1 : (c > MAX_LINK_CTAS ? MAX_LINK_CTAS : c));
+        }
         h->links = (int32_t *)dev_alloc(h, sizeof(int32_t) * (total > 0 ? total : 1));
         if (!h->links) {
             dev_free(h, blk);
@@ -605,7 +619,7 @@ lbm_status lbm_step(lbm_ctx *h, int n)
 lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, double *fx, double *fy)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
-    if (scheme < 0 || scheme > 3) return set_err(h, LBM_EINVAL, "unknown scheme %d", scheme);
+    if (scheme < 0 || scheme > 4) return set_err(h, LBM_EINVAL, "unknown scheme %d", scheme);
     if (count < 0 || first < 0 || first + count > h->t)
         return set_err(h, LBM_EINVAL, "steps [%ld, %ld) outside [0, %lld)", first, first + count, h->t);
     if (count == 0) return LBM_OK;
@@ -616,22 +630,23 @@ lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, doub
         lbm_status st = finalize_drtt(h);
         if (st != LBM_OK) return st;
     }
-    std::vector<double> rows((size_t)count * 8);
+    const size_t R = SERIES_ROW;
+    std::vector<double> rows((size_t)count * R);
     if (h->record_series) {
-        CK(h, cudaMemcpyAsync(rows.data(), h->series + 8 * first, sizeof(double) * 8 * count,
+        CK(h, cudaMemcpyAsync(rows.data(), h->series + R * first, sizeof(double) * R * count,
                               cudaMemcpyDeviceToHost, h->stream),
            "D2H series");
     } else {
         for (long k = 0; k < count; ++k)
-            CK(h, cudaMemcpyAsync(rows.data() + 8 * k, h->series + 8 * ((first + k) & 1),
-                                  sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream),
+            CK(h, cudaMemcpyAsync(rows.data() + R * k, h->series + R * ((first + k) & 1),
+                                  sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream),
                "D2H series");
     }
     CK(h, cudaStreamSynchronize(h->stream), "sync");
-    const int col = scheme == LBM_FORCE_MEA_A ? 0 : scheme == LBM_FORCE_MEA_B ? 2 : scheme == LBM_FORCE_DRTT ? 4 : 6;
+    const int col = 2 * scheme;  // row: A, B, DRTT, A', defect (x, y each)
     for (long k = 0; k < count; ++k) {
-        fx[k] = rows[8 * k + col];
-        fy[k] = rows[8 * k + col + 1];
+        fx[k] = rows[R * k + col];
+        fy[k] = rows[R * k + col + 1];
     }
     return LBM_OK;
 }

@@ -12,9 +12,12 @@
 //                bounce-back path);
 //   links        int32 [L], n*8 + (i-1), ascending;
 //   inlet        [9][ny] storage-type inlet populations feq(rho0, u_in(y));
-//   partials     double [n_cv_tiles][4] per-tile J(t) and gained-lost(t);
-//   series       double [steps][4 schemes][2] forces;
-//   carry        double [8]: J(t-1), GL(t-1), flag, spare;  step counter int64.
+//   partials     double [n_cv_tiles][6] per-tile J(t) on the pre- and on the
+//                post-collision state, and gained-minus-lost(t);
+//   link_partials double [LINK_CTAS][12] per-CTA rows of the link kernel;
+//   series       double [steps][10]: A, B, DRTT, A', momentum defect (x, y);
+//   carry        double [8]: J_post(t-1), GL(t-1), flag;  step counter int64;
+//   ticket       uint32 arrival counter of the link kernel's CTAs.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -31,7 +34,11 @@ constexpr int TILE_X = 128;
 constexpr int TILE_ROWS = 4;
 constexpr int ROWS_PER_THREAD = TILE_ROWS / 2;
 constexpr int PITCH_ALIGN = 64;
-constexpr int LINK_THREADS = 1024;
+constexpr int LINK_THREADS = 128;
+constexpr int MAX_LINK_CTAS = 148;
+constexpr int CV_PARTIAL = 6;
+constexpr int LINK_PARTIAL = 12;
+constexpr int SERIES_ROW = 10;
 
 // ---- D2Q9 (Section II, Table tabD2Q9) as compile-time functions ----
 __host__ __device__ constexpr int cx(int i) {
@@ -87,7 +94,7 @@ struct StepArgs {
     const uint16_t *nbits;
     const uint8_t *tile_flag;
     const void *inlet;       // [9][ny]
-    double *partials;        // [n_cv_tiles][4]
+    double *partials;        // [n_cv_tiles][CV_PARTIAL]
     int *status;             // [0] flags, [1] first bad step
     const long long *step_ctr;
     long long plane;         // elements per plane = ny * pitch
@@ -108,8 +115,11 @@ struct LinkArgs {
     long long nlinks;
     const double *partials;
     int n_partials;
+    double *link_partials;   // [n_ctas][LINK_PARTIAL]
+    unsigned int *ticket;
+    int n_ctas;
     double *series;
-    double *carry;           // J(t-1)[2], GL(t-1)[2], have_prev
+    double *carry;           // J_post(t-1)[2], GL(t-1)[2], have_prev
     long long *step_ctr;
     long long plane;
     int nx, ny, pitch, periodic, precollision;

@@ -12,7 +12,8 @@
 // k_link_force: one CTA walks the fluid-solid link list and reduces the
 //   momentum exchange of step t for algorithms A, A' and B (Eqs. MEA, rtt4,
 //   rtt5), folds the control-volume partials into J(t), and completes
-//   DRTT(t-1) = J(t-1) - J(t) + GL(t-1) (Eq. rtt7).
+//   DRTT(t-1) = J(t-1) - J(t) + GL(t-1) (Eq. rtt7).  Several CTAs share the
+//   links; the last one to finish reduces their rows in a fixed order.
 //
 // All reductions run in FP64 in a fixed order (warp shuffles, then a fixed
 // tree over warps), so results are deterministic for a given grid.
@@ -52,7 +53,7 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV])
 // CHECKED: the tile holds solid nodes (bounce-back tests needed).
 // ---------------------------------------------------------------------------
 template <int S, bool CHECKED, bool MOMENTUM_ONLY>
-__device__ __forceinline__ void node_update(const StepArgs &a, int x, int y, double (&acc)[4],
+__device__ __forceinline__ void node_update(const StepArgs &a, int x, int y, double (&acc)[6],
                                             bool cvtile, bool &bad)
 {
     using ST = typename Traits<S>::store_t;
@@ -135,8 +136,24 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int x, int y, dou
     if (!cvtile) return;
     const bool inV = x >= a.cv[0] && x <= a.cv[1] && y >= a.cv[2] && y <= a.cv[3];
     if (inV) {
-        acc[0] += (double)jx;
-        acc[1] += (double)jy;
+        // J(t) of the box (Eq. rtt1).  Sums of stored-precision values taken in
+        // FP64 are exact for FP32 and FP16 storage (at most ~42 significant bits).
+        // acc[0..1]: on the pre-collision f(t), as the Appendix orders it;
+        // acc[2..3]: on the stored post-collision ft(t) less the body-force
+        // momentum g.  BGK collision conserves momentum, so both are J(t) in
+        // exact arithmetic; the second is the one whose streamed values make
+        // up J(t+1), so it carries no rounding defect of the collision.
+        double d[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = (double)f[i];
+        acc[0] += ((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7]);
+        acc[1] += ((d[2] - d[4]) + (d[5] + d[6])) - (d[7] + d[8]);
+        if (!MOMENTUM_ONLY) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) d[i] = (double)ftr[i];
+            acc[2] += (((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7])) - a.gx;
+            acc[3] += (((d[2] - d[4]) + (d[5] + d[6])) - (d[7] + d[8])) - a.gy;
+        }
     }
     if (MOMENTUM_ONLY) return;
     // post-collision populations crossing the box surface: + entering, - leaving
@@ -155,8 +172,8 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int x, int y, dou
         double v = (double)ftr[i];
         if (DEV) v += wgt<double>(i) * a.rho0;
         if (inV) v = -v;
-        acc[2] += cx(i) * v;
-        acc[3] += cy(i) * v;
+        acc[4] += cx(i) * v;
+        acc[5] += cy(i) * v;
     }
 }
 
@@ -167,7 +184,7 @@ __global__ void __launch_bounds__(TILE_X * 2) k_collide_stream(StepArgs a)
     const int x = tx * TILE_X + threadIdx.x;
     const bool checked = a.precollision || a.tile_flag[(long long)ty * a.tiles_x + tx] != 0;
     const bool cvtile = tx >= a.cvt[0] && tx <= a.cvt[1] && ty >= a.cvt[2] && ty <= a.cvt[3];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     bool bad = false;
     const int y0 = ty * TILE_ROWS + threadIdx.y * ROWS_PER_THREAD;
     if (x < a.nx) {
@@ -182,14 +199,12 @@ __global__ void __launch_bounds__(TILE_X * 2) k_collide_stream(StepArgs a)
         }
     }
     if (cvtile) {
-        block_reduce<4, TILE_X * 2>(acc);
+        block_reduce<6, TILE_X * 2>(acc);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const int slot = (ty - a.cvt[2]) * (a.cvt[1] - a.cvt[0] + 1) + (tx - a.cvt[0]);
-            double *p = a.partials + 4 * (long long)slot;
-            p[0] = acc[0];
-            p[1] = acc[1];
-            p[2] = MOMENTUM_ONLY ? 0.0 : acc[2];
-            p[3] = MOMENTUM_ONLY ? 0.0 : acc[3];
+            double *p = a.partials + CV_PARTIAL * (long long)slot;
+#pragma unroll
+            for (int k = 0; k < CV_PARTIAL; ++k) p[k] = (MOMENTUM_ONLY && k >= 2) ? 0.0 : acc[k];
         }
     }
     if (!MOMENTUM_ONLY) {
@@ -221,7 +236,13 @@ cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, i
 }
 
 // ---------------------------------------------------------------------------
-// Link force + finalisation, one CTA of LINK_THREADS threads.
+// Link force + finalisation.  LINK_CTAS CTAs of LINK_THREADS threads share the
+// links (contiguous chunks) and the control-volume partials; each writes one
+// FP64 partial row.  The last CTA to finish (atomic ticket) sums the rows in
+// slot order, so the result does not depend on which CTA finishes last, and
+// completes the step's series row and the DRTT of the previous step.
+// Series row t: A(2) B(2) DRTT(2) A'(2) defect(2), where defect is the
+// collision's momentum defect inside the box, J_pre(t) - J_post(t).
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
@@ -231,9 +252,15 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
     const ST *__restrict__ src = (const ST *)a.src;
     const ST *__restrict__ dst = (const ST *)a.dst;
     const long long plane = a.plane;
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // A, B, A' (x, y)
+    // v: A(2), B(2), A'(2), J_pre(2), J_post(2), GL(2)
+    double v[LINK_PARTIAL];
+#pragma unroll
+    for (int k = 0; k < LINK_PARTIAL; ++k) v[k] = 0.0;
+    const long long per = (a.nlinks + gridDim.x - 1) / gridDim.x;
+    const long long k0 = per * blockIdx.x;
+    const long long k1 = k0 + per < a.nlinks ? k0 + per : a.nlinks;
     if (!a.drtt_only) {
-        for (long long k = threadIdx.x; k < a.nlinks; k += LINK_THREADS) {
+        for (long long k = k0 + threadIdx.x; k < k1; k += LINK_THREADS) {
             const int l = a.links[k];
             const int n = l >> 3;
             const int i = (l & 7) + 1;
@@ -273,42 +300,65 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
             v[5] += ey * (fi + ft);
         }
     }
-    block_reduce<6, LINK_THREADS>(v);
-    double j[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int s = threadIdx.x; s < a.n_partials; s += LINK_THREADS) {
-        const double *p = a.partials + 4 * (long long)s;
-        j[0] += p[0];
-        j[1] += p[1];
-        j[2] += p[2];
-        j[3] += p[3];
+    {
+        const int per_p = (a.n_partials + gridDim.x - 1) / gridDim.x;
+        const int p0 = per_p * blockIdx.x;
+        const int p1 = p0 + per_p < a.n_partials ? p0 + per_p : a.n_partials;
+        for (int s = p0 + threadIdx.x; s < p1; s += LINK_THREADS) {
+            const double *p = a.partials + CV_PARTIAL * (long long)s;
+#pragma unroll
+            for (int k = 0; k < CV_PARTIAL; ++k) v[6 + k] += p[k];
+        }
     }
-    block_reduce<4, LINK_THREADS>(j);
+    block_reduce<LINK_PARTIAL, LINK_THREADS>(v);
+    __shared__ bool last;
     if (threadIdx.x == 0) {
+        double *row = a.link_partials + LINK_PARTIAL * (long long)blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) row[k] = v[k];
+        __threadfence();
+        const unsigned int ticket = atomicAdd(a.ticket, 1u);
+        last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double w[LINK_PARTIAL];
+#pragma unroll
+    for (int k = 0; k < LINK_PARTIAL; ++k) w[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += LINK_THREADS) {
+        const volatile double *row = a.link_partials + LINK_PARTIAL * (long long)b;
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) w[k] += row[k];
+    }
+    block_reduce<LINK_PARTIAL, LINK_THREADS>(w);
+    if (threadIdx.x == 0) {
+        *a.ticket = 0u;
         const long long t = *a.step_ctr;
-        auto row = [&](long long s) { return a.series + 8 * (a.record_series ? s : (s & 1)); };
-        if (a.drtt_only) {
-            if (a.carry[4] != 0.0 && t >= 1) {
-                double *r = row(t - 1);
-                r[4] = (a.carry[0] - j[0]) + a.carry[2];
-                r[5] = (a.carry[1] - j[1]) + a.carry[3];
-            }
-        } else {
+        auto row = [&](long long s) {
+            return a.series + SERIES_ROW * (a.record_series ? s : (s & 1));
+        };
+        // DRTT(t-1) = J(t-1) - J(t) + (gained - lost)(t-1), Eq. rtt7, with
+        // J(t-1) on the post-collision state and J(t) on the pre-collision one
+        if (a.carry[4] != 0.0 && t >= 1) {
+            double *q = row(t - 1);
+            q[4] = (a.carry[0] - w[6]) + a.carry[2];
+            q[5] = (a.carry[1] - w[7]) + a.carry[3];
+        }
+        if (!a.drtt_only) {
             double *r = row(t);
-            r[0] = v[0];
-            r[1] = v[1];
-            r[2] = v[2];
-            r[3] = v[3];
-            r[6] = v[4];
-            r[7] = v[5];
-            if (a.carry[4] != 0.0 && t >= 1) {
-                double *q = row(t - 1);
-                q[4] = (a.carry[0] - j[0]) + a.carry[2];
-                q[5] = (a.carry[1] - j[1]) + a.carry[3];
-            }
-            a.carry[0] = j[0];
-            a.carry[1] = j[1];
-            a.carry[2] = j[2];
-            a.carry[3] = j[3];
+            r[0] = w[0];
+            r[1] = w[1];
+            r[2] = w[2];
+            r[3] = w[3];
+            r[6] = w[4];
+            r[7] = w[5];
+            r[8] = w[6] - w[8];
+            r[9] = w[7] - w[9];
+            a.carry[0] = w[8];
+            a.carry[1] = w[9];
+            a.carry[2] = w[10];
+            a.carry[3] = w[11];
             a.carry[4] = 1.0;
             *a.step_ctr = t + 1;
         }
@@ -317,11 +367,12 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
 
 cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st)
 {
+    const int grid = a.n_ctas;
     switch (storage) {
-    case LBM_F64: k_link_force<LBM_F64><<<1, LINK_THREADS, 0, st>>>(a); break;
-    case LBM_F32: k_link_force<LBM_F32><<<1, LINK_THREADS, 0, st>>>(a); break;
-    case LBM_F32_DEV: k_link_force<LBM_F32_DEV><<<1, LINK_THREADS, 0, st>>>(a); break;
-    default: k_link_force<LBM_F16_DEV><<<1, LINK_THREADS, 0, st>>>(a); break;
+    case LBM_F64: k_link_force<LBM_F64><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    case LBM_F32: k_link_force<LBM_F32><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    case LBM_F32_DEV: k_link_force<LBM_F32_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    default: k_link_force<LBM_F16_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }

