@@ -197,6 +197,34 @@ lbm_status lbm_kernel_times(lbm_ctx *h, double *ms, long *launches, int reset);
 /* Kernel launches made by the handle since creation (all kernels). */
 long lbm_launch_count(const lbm_ctx *h);
 
+/* The fluid-solid link list of a mask that already lives in device memory,
+ * built without allocating any memory.  The paper has no counterpart: this is
+ * a service entry point of this library.  It serves callers that must not
+ * allocate device memory themselves or through this library: code that runs
+ * inside a host application owning a fixed device-memory budget or its own
+ * memory pool, plug-ins whose host forbids cudaMalloc, and latency-sensitive
+ * callers that cannot accept the device-wide synchronisation cudaMalloc and
+ * cudaFree may cause.  The result equals lbm_links() on a handle created from
+ * the same mask and boundary kind (same list, same order).
+ *   d_mask      device pointer, uint8 [ny][nx], nonzero = solid; caller-owned.
+ *   periodic_x  1: x wraps (LBM_BC_PERIODIC), 0: it does not (LBM_BC_CHANNEL);
+ *               y always wraps.
+ *   d_links     device pointer to cap int32 entries, caller-owned; receives
+ *               n*8 + (i-1) in ascending order (at most cap entries).
+ *   count       host pointer; receives the total number of links.
+ *   cuda_stream cudaStream_t the work is queued on (NULL: legacy default);
+ *               the call returns after that stream has finished the work.
+ * Limit: nx*ny <= 2^26 nodes; larger grids return EINVAL.  Working memory is
+ * one fixed static device array of 256 KB, present on every device that loads
+ * the library until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with the device current);
+ * make that first call before any stream capture.  All calls on a device share
+ * the array, so calls whose GPU work overlaps (other host threads, other
+ * streams) race and must be serialised by the caller.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine. */
+lbm_status lbm_links_noalloc(const uint8_t *d_mask, int nx, int ny, int periodic_x,
+                             int32_t *d_links, long cap, long *count, void *cuda_stream);
+
 /* Message of the last failed call on h (or of the calling thread when h is NULL). */
 const char *lbm_last_error(const lbm_ctx *h);
 

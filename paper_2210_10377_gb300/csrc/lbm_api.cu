@@ -23,6 +23,8 @@ constexpr int TIMING_BATCH = 64;
 
 }  // namespace
 
+void gblbm::set_thread_error(const char *msg) { g_thread_err = msg; }
+
 struct lbm_ctx {
     int nx = 0, ny = 0, pitch = 0, periodic = 0, storage = 0;
     double tau = 0, omega = 0, rho0 = 1, g[2] = {0, 0};

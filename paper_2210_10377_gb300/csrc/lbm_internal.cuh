@@ -128,6 +128,9 @@ struct LinkArgs {
     double rho0;
 };
 
+// Message returned by lbm_last_error(NULL) on the calling thread.
+void set_thread_error(const char *msg);
+
 // ---- launchers (defined in the .cu files) ----
 cudaError_t launch_naca_mask(uint8_t *mask, int nx, int ny, double chord, double thickness,
                              double ca, double sa, double xc, double yc, int closed_te,
