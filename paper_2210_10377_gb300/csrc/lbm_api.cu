@@ -51,6 +51,7 @@ struct lbm_ctx {
     double *link_partials = nullptr;
     unsigned int *ticket = nullptr;
     int link_ctas = 1;
+    double link_base[2] = {0, 0}, flux_base[2] = {0, 0};
     double *series = nullptr;
     long long series_cap = 0;
     double *carry = nullptr;     // [8]
@@ -168,6 +169,60 @@ void auto_cv(const uint8_t *mask, int nx, int ny, int periodic, int *cv)
     cv[3] = y1;
 }
 
+// Fixed momentum of the deviation base w_i rho0 (geometry only):
+//   link_base = 2 rho0 sum over links (x_f, i) of c_i w_i (each link's
+//   populations f_i and f_opp carry w_i rho0 each; so does the bounced ft_i);
+//   flux_base = rho0 sum over box-surface crossings of +-c_i w_i.
+// Links are enumerated from the solid nodes, crossings from the box edge.
+void base_sums(const uint8_t *mask, int nx, int ny, int periodic, const int *cv, double rho0,
+               double *link_base, double *flux_base)
+{
+    const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    auto W = [](int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); };
+    auto solid = [&](int x, int y) { return mask[(size_t)y * nx + x] != 0; };
+    auto wrap = [&](int &x, int &y) {
+        y = (y % ny + ny) % ny;
+        if (x < 0 || x >= nx) {
+            if (!periodic) return false;
+            x = (x % nx + nx) % nx;
+        }
+        return true;
+    };
+    double lb[2] = {0, 0};
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (!solid(x, y)) continue;
+            for (int i = 1; i < 9; ++i) {  // fluid x_f = s - c_i with x_f + c_i = s
+                int xf = x - CX[i], yf = y - CY[i];
+                if (!wrap(xf, yf) || solid(xf, yf)) continue;
+                lb[0] += CX[i] * W(i);
+                lb[1] += CY[i] * W(i);
+            }
+        }
+    double fb[2] = {0, 0};
+    auto inbox = [&](int x, int y) { return x >= cv[0] && x <= cv[1] && y >= cv[2] && y <= cv[3]; };
+    for (int y = cv[2] - 1; y <= cv[3] + 1; ++y)
+        for (int x = cv[0] - 1; x <= cv[1] + 1; ++x) {
+            int xn = x, yn = y;
+            if (!wrap(xn, yn)) continue;
+            if (x != xn || y != yn) continue;  // each node once, in unwrapped position
+            if (solid(xn, yn)) continue;
+            const bool in = inbox(xn, yn);
+            for (int i = 1; i < 9; ++i) {
+                int x2 = xn + CX[i], y2 = yn + CY[i];
+                if (!wrap(x2, y2) || solid(x2, y2) || inbox(x2, y2) == in) continue;
+                const double s = in ? -1.0 : 1.0;
+                fb[0] += s * CX[i] * W(i);
+                fb[1] += s * CY[i] * W(i);
+            }
+        }
+    link_base[0] = 2.0 * rho0 * lb[0];
+    link_base[1] = 2.0 * rho0 * lb[1];
+    flux_base[0] = rho0 * fb[0];
+    flux_base[1] = rho0 * fb[1];
+}
+
 bool range_ok(int lo, int hi, int n, bool whole_allowed)
 {
     if (lo > hi) return false;
@@ -229,6 +284,8 @@ LinkArgs link_args(lbm_ctx *h, int src, int precollision, int drtt_only)
     a.record_series = h->record_series;
     a.drtt_only = drtt_only;
     a.rho0 = h->rho0;
+    memcpy(a.link_base, h->link_base, sizeof(a.link_base));
+    memcpy(a.flux_base, h->flux_base, sizeof(a.flux_base));
     return a;
 }
 
@@ -436,6 +493,8 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     h->g[0] = bc.body_force[0];
     h->g[1] = bc.body_force[1];
     memcpy(h->cv, cv, sizeof(cv));
+    if (bc.storage == LBM_F32_DEV || bc.storage == LBM_F16_DEV)
+        base_sums(mask, nx, ny, periodic, cv, bc.rho0, h->link_base, h->flux_base);
     h->record_series = bc.record_series ? 1 : 0;
     h->alloc_fn = bc.alloc;
     h->free_fn = bc.free;

@@ -12,9 +12,10 @@
 //                bounce-back path);
 //   links        int32 [L], n*8 + (i-1), ascending;
 //   inlet        [9][ny] storage-type inlet populations feq(rho0, u_in(y));
-//   partials     double [n_cv_tiles][6] per-tile J(t) on the pre- and on the
-//                post-collision state, and gained-minus-lost(t);
-//   link_partials double [LINK_CTAS][12] per-CTA rows of the link kernel;
+//   partials     [n_cv_tiles][6] per-tile J(t) on the pre- and on the
+//                post-collision state, and gained-minus-lost(t); FP64 for FP64
+//                storage, float-float pairs otherwise (8 bytes either way);
+//   link_partials [n_ctas][12] per-CTA rows of the link kernel, same types;
 //   series       double [steps][10]: A, B, DRTT, A', momentum defect (x, y);
 //   carry        double [8]: J_post(t-1), GL(t-1), flag;  step counter int64;
 //   ticket       uint32 arrival counter of the link kernel's CTAs.
@@ -28,11 +29,10 @@
 
 namespace gblbm {
 
-// Collide-stream tile: 128 nodes along x by TILE_ROWS rows; one CTA of
-// 128 x 2 threads, each thread walks TILE_ROWS/2 rows of one column.
+// Collide-stream tile: 128 nodes along x by TILE_ROWS rows; one CTA per tile,
+// 128 threads along x, each thread walking a few rows of one column.
 constexpr int TILE_X = 128;
 constexpr int TILE_ROWS = 4;
-constexpr int ROWS_PER_THREAD = TILE_ROWS / 2;
 constexpr int PITCH_ALIGN = 64;
 constexpr int LINK_THREADS = 128;
 constexpr int MAX_LINK_CTAS = 148;
@@ -126,6 +126,8 @@ struct LinkArgs {
     int record_series;
     int drtt_only;           // finalise DRTT(T-1) from a momentum-only pass
     double rho0;
+    double link_base[2];     // deviation storage: 2 rho0 sum_links c_i w_i
+    double flux_base[2];     // deviation storage: rho0 (sum_in - sum_out) c_i w_i
 };
 
 // Message returned by lbm_last_error(NULL) on the calling thread.

@@ -7,31 +7,106 @@
 //   feq (second-order equilibrium, theta0 = 1/3) and stores ft(x, t).  The
 //   channel inlet column stores feq(rho0, u_in(y)); the outlet column collides
 //   the populations of column nx-2 (zero-gradient copy).  Tiles that cover the
-//   DRTT control volume also reduce J(t) (Eq. rtt1, pre-collision) and the
-//   gained-minus-lost flux of ft(t) through the box surface (Eq. rtt7).
-// k_link_force: one CTA walks the fluid-solid link list and reduces the
-//   momentum exchange of step t for algorithms A, A' and B (Eqs. MEA, rtt4,
-//   rtt5), folds the control-volume partials into J(t), and completes
-//   DRTT(t-1) = J(t-1) - J(t) + GL(t-1) (Eq. rtt7).  Several CTAs share the
-//   links; the last one to finish reduces their rows in a fixed order.
+//   DRTT control volume also reduce J(t) (Eq. rtt1) and the gained-minus-lost
+//   flux of ft(t) through the box surface (Eq. rtt7).
+// k_link_force: CTAs share the fluid-solid link list and reduce the momentum
+//   exchange of step t for algorithms A, A' and B (Eqs. MEA, rtt4, rtt5), fold
+//   the control-volume partials into J(t), and the last CTA to finish completes
+//   DRTT(t-1) = J(t-1) - J(t) + GL(t-1) (Eq. rtt7).
 //
-// All reductions run in FP64 in a fixed order (warp shuffles, then a fixed
-// tree over warps), so results are deterministic for a given grid.
+// Reductions are deterministic (fixed trees, no floating-point atomics).  For
+// FP64 storage they run in FP64; for FP32 and FP16 storage in compensated FP32
+// pairs ("float-float", about 48 significant bits), which keeps the slow FP64
+// units of this GPU out of the hot path.  Sums of a node's populations are
+// exact in float-float.
 #include "lbm_internal.cuh"
 
 namespace gblbm {
 
-// FP64 block reduction; the result is valid in thread 0.  NT threads, NT % 32 == 0.
-template <int NV, int NT>
-__device__ __forceinline__ void block_reduce(double (&v)[NV])
+// ---- float-float arithmetic (error-free sums of FP32 values) ----
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
 {
-    __shared__ double sm[NT / 32][NV];
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_addf(ff a, float b)
+{
+    const ff s = ff_two_sum(a.hi, b);
+    return ff_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff operator-(ff a) { return {-a.hi, -a.lo}; }
+
+// Accumulator per storage: FP64 for FP64 storage, float-float otherwise.
+template <int S> struct AccOf {
+    using type = ff;
+};
+template <> struct AccOf<LBM_F64> {
+    using type = double;
+};
+
+__device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void acc_zero(ff &a) { a = {0.0f, 0.0f}; }
+__device__ __forceinline__ void acc_add(double &a, double b) { a += b; }
+__device__ __forceinline__ void acc_add(ff &a, ff b) { a = ff_add(a, b); }
+__device__ __forceinline__ double acc_double(double a) { return a; }
+__device__ __forceinline__ double acc_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ ff shfl_down(ff v, int d)
+{
+    return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+
+// Signed sums of a node's populations: x-momentum f1 - f3 + f5 - f6 - f7 + f8,
+// y-momentum f2 - f4 + f5 + f6 - f7 - f8.  Exact in float-float for FP32 values.
+__device__ __forceinline__ double mom_x(const double *f)
+{
+    return ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
+}
+__device__ __forceinline__ double mom_y(const double *f)
+{
+    return ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
+}
+__device__ __forceinline__ ff mom_x(const float *f)
+{
+    ff s = ff_two_sum(f[1], -f[3]);
+    s = ff_addf(s, f[5]);
+    s = ff_addf(s, -f[6]);
+    s = ff_addf(s, -f[7]);
+    return ff_addf(s, f[8]);
+}
+__device__ __forceinline__ ff mom_y(const float *f)
+{
+    ff s = ff_two_sum(f[2], -f[4]);
+    s = ff_addf(s, f[5]);
+    s = ff_addf(s, f[6]);
+    s = ff_addf(s, -f[7]);
+    return ff_addf(s, -f[8]);
+}
+__device__ __forceinline__ double as_acc(double v, double) { return v; }
+__device__ __forceinline__ ff as_acc(float v, ff) { return {v, 0.0f}; }
+
+// Block reduction; the result is valid in thread 0.  NT threads, NT % 32 == 0.
+template <typename A, int NV, int NT>
+__device__ __forceinline__ void block_reduce(A (&v)[NV])
+{
+    __shared__ A sm[NT / 32][NV];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
+    for (int d = 16; d > 0; d >>= 1)
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
+        for (int k = 0; k < NV; ++k) acc_add(v[k], shfl_down(v[k], d));
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NV; ++k) sm[warp][k] = v[k];
@@ -39,61 +114,76 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV])
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double s = lane < NT / 32 ? sm[lane][k] : 0.0;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-            v[k] = s;
+            if (lane < NT / 32)
+                v[k] = sm[lane][k];
+            else
+                acc_zero(v[k]);
         }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc_add(v[k], shfl_down(v[k], d));
     }
     __syncthreads();
 }
 
+// Rows per thread of the 128 x TILE_ROWS collide-stream tile, per storage:
+// enough independent loads in flight per thread to cover HBM latency.
+template <int S> struct RowsPerThread {
+    static constexpr int value = 2;
+};
+template <> struct RowsPerThread<LBM_F64> {
+    static constexpr int value = 1;
+};
+template <> struct RowsPerThread<LBM_F16_DEV> {
+    static constexpr int value = 4;
+};
+
 // ---------------------------------------------------------------------------
-// Fused pull-stream + bounce-back + boundary + BGK collision for one node.
+// Fused pull-stream + bounce-back + boundary + BGK collision for the RPT rows
+// of one thread: all loads first, then collision and stores row by row.
 // CHECKED: the tile holds solid nodes (bounce-back tests needed).
 // ---------------------------------------------------------------------------
-template <int S, bool CHECKED, bool MOMENTUM_ONLY>
-__device__ __forceinline__ void node_update(const StepArgs &a, int x, int y, double (&acc)[6],
-                                            bool cvtile, bool &bad)
+template <int S, bool CHECKED, bool MOMENTUM_ONLY, int RPT>
+__device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
+                                              typename AccOf<S>::type (&acc)[6], bool cvtile,
+                                              bool &bad)
 {
     using ST = typename Traits<S>::store_t;
     using T = typename Traits<S>::comp_t;
+    using A = typename AccOf<S>::type;
     constexpr bool DEV = Traits<S>::dev;
     const ST *__restrict__ src = (const ST *)a.src;
     ST *__restrict__ dst = (ST *)a.dst;
     const long long plane = a.plane;
-    const long long idx = (long long)y * a.pitch + x;
     const bool channel = !a.periodic;
-    const uint16_t nb = CHECKED ? a.nbits[idx] : (uint16_t)0;
-    if (nb & 1) return;  // solid nodes are not updated
-
-    T f[9];
-    T ftr[9];
-    T jx = T(0), jy = T(0);
     const bool inlet = channel && x == 0;
-    if (inlet) {
-        if (MOMENTUM_ONLY) return;  // the inlet column never lies in the control volume
-        const ST *in = (const ST *)a.inlet;
+    if (inlet && MOMENTUM_ONLY) return;  // the inlet column never lies in the control volume
+    // the outlet column x = nx-1 takes the populations of column nx-2
+    const int xs = (channel && x == a.nx - 1 && !a.precollision) ? a.nx - 2 : x;
+    int xm = xs - 1, xp = xs + 1;
+    if (!channel) {
+        xm = xm < 0 ? xm + a.nx : xm;
+        xp = xp >= a.nx ? xp - a.nx : xp;
+    }
+
+    T f[RPT][9];
+    uint16_t nb[RPT];
+    bool live[RPT];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            ST sv = in[i * a.ny + y];
-            dst[i * plane + idx] = sv;
-            ftr[i] = to_comp(sv);
-        }
-    } else {
+    for (int r = 0; r < RPT; ++r) {
+        const int y = y0 + r;
+        live[r] = y < a.ny;
+        const long long idx = (long long)y * a.pitch + x;
+        nb[r] = (CHECKED && live[r]) ? a.nbits[idx] : (uint16_t)0;
+        if (nb[r] & 1) live[r] = false;  // solid nodes are not updated
+        if (!live[r] || inlet) continue;
         if (a.precollision) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = to_comp(src[i * plane + idx]);
+            for (int i = 0; i < 9; ++i) f[r][i] = to_comp(src[i * plane + idx]);
         } else {
-            // the outlet column x = nx-1 takes the populations of column nx-2
-            const int xs = (channel && x == a.nx - 1) ? a.nx - 2 : x;
             const long long sidx = (long long)y * a.pitch + xs;
-            const uint16_t nbs = CHECKED ? (xs == x ? nb : a.nbits[sidx]) : (uint16_t)0;
-            int xm = xs - 1, xp = xs + 1;
-            if (!channel) {
-                xm = xm < 0 ? xm + a.nx : xm;
-                xp = xp >= a.nx ? xp - a.nx : xp;
-            }
+            const uint16_t nbs = CHECKED ? (xs == x ? nb[r] : a.nbits[sidx]) : (uint16_t)0;
             const int ym = y == 0 ? a.ny - 1 : y - 1;
             const int yp = y == a.ny - 1 ? 0 : y + 1;
 #pragma unroll
@@ -101,18 +191,35 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int x, int y, dou
                 const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : xs);
                 const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
                 if (CHECKED && (nbs & (1u << opp(i))))
-                    f[i] = to_comp(src[opp(i) * plane + sidx]);
+                    f[r][i] = to_comp(src[opp(i) * plane + sidx]);
                 else
-                    f[i] = to_comp(src[i * plane + (long long)sy * a.pitch + sx]);
+                    f[r][i] = to_comp(src[i * plane + (long long)sy * a.pitch + sx]);
             }
         }
-        jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
-        jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
-        if (!MOMENTUM_ONLY) {
+    }
+
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        if (!live[r]) continue;
+        const int y = y0 + r;
+        const long long idx = (long long)y * a.pitch + x;
+        T ftr[9];
+        if (inlet) {
+            const ST *in = (const ST *)a.inlet;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const ST sv = in[i * a.ny + y];
+                dst[i * plane + idx] = sv;
+                ftr[i] = to_comp(sv);
+            }
+        } else if (!MOMENTUM_ONLY) {
             // rho = R0 + sum f (R0 = rho0 for deviation storage, 0 otherwise);
             // feq - w R0 = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
+            const T *g = f[r];
             const T R0 = DEV ? (T)a.rho0 : T(0);
-            const T drho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+            const T jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
+            const T jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
+            const T drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
             const T rho = R0 + drho;
             if (!(rho > T(0))) bad = true;
             const T inv = T(1) / rho;
@@ -124,87 +231,88 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int x, int y, dou
             for (int i = 0; i < 9; ++i) {
                 const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
                 const T geq = wgt<T>(i) * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq));
-                T v = f[i] + om * (geq - f[i]);
+                T v = g[i] + om * (geq - g[i]);
                 if (i != 0) v += T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy);
                 const ST sv = to_store<ST>(v);
                 dst[i * plane + idx] = sv;
                 ftr[i] = to_comp(sv);
             }
         }
-    }
-
-    if (!cvtile) return;
-    const bool inV = x >= a.cv[0] && x <= a.cv[1] && y >= a.cv[2] && y <= a.cv[3];
-    if (inV) {
-        // J(t) of the box (Eq. rtt1).  Sums of stored-precision values taken in
-        // FP64 are exact for FP32 and FP16 storage (at most ~42 significant bits).
-        // acc[0..1]: on the pre-collision f(t), as the Appendix orders it;
-        // acc[2..3]: on the stored post-collision ft(t) less the body-force
-        // momentum g.  BGK collision conserves momentum, so both are J(t) in
-        // exact arithmetic; the second is the one whose streamed values make
-        // up J(t+1), so it carries no rounding defect of the collision.
-        double d[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = (double)f[i];
-        acc[0] += ((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7]);
-        acc[1] += ((d[2] - d[4]) + (d[5] + d[6])) - (d[7] + d[8]);
-        if (!MOMENTUM_ONLY) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) d[i] = (double)ftr[i];
-            acc[2] += (((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7])) - a.gx;
-            acc[3] += (((d[2] - d[4]) + (d[5] + d[6])) - (d[7] + d[8])) - a.gy;
+        if (!cvtile) continue;
+        const bool inV = x >= a.cv[0] && x <= a.cv[1] && y >= a.cv[2] && y <= a.cv[3];
+        if (inV) {
+            // J(t) of the box (Eq. rtt1).  acc[0..1]: on the pre-collision f(t),
+            // as the Appendix orders it; acc[2..3]: on the stored post-collision
+            // ft(t) less the body-force momentum g.  BGK collision conserves
+            // momentum, so both are J(t) in exact arithmetic; the second is the
+            // one whose streamed values make up J(t+1), so it carries no rounding
+            // defect of the reduced-precision collision.  (Deviation storage: the
+            // base w_i rho0 carries no momentum, sum_i c_i w_i = 0.)
+            acc_add(acc[0], mom_x(f[r]));
+            acc_add(acc[1], mom_y(f[r]));
+            if (!MOMENTUM_ONLY) {
+                acc_add(acc[2], mom_x(ftr));
+                acc_add(acc[3], mom_y(ftr));
+                acc_add(acc[2], as_acc(-(T)a.gx, A()));
+                acc_add(acc[3], as_acc(-(T)a.gy, A()));
+            }
         }
-    }
-    if (MOMENTUM_ONLY) return;
-    // post-collision populations crossing the box surface: + entering, - leaving
+        if (MOMENTUM_ONLY) continue;
+        // post-collision populations crossing the box surface: + entering, - leaving
+        // (deviation storage: the base parts w_i rho0 are added once by the link
+        // kernel, they do not change from step to step)
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        int x2 = x + cx(i);
-        if (x2 < 0 || x2 >= a.nx) {
-            if (channel) continue;
-            x2 = x2 < 0 ? x2 + a.nx : x2 - a.nx;
+        for (int i = 1; i < 9; ++i) {
+            int x2 = x + cx(i);
+            if (x2 < 0 || x2 >= a.nx) {
+                if (channel) continue;
+                x2 = x2 < 0 ? x2 + a.nx : x2 - a.nx;
+            }
+            int y2 = y + cy(i);
+            y2 = y2 < 0 ? y2 + a.ny : (y2 >= a.ny ? y2 - a.ny : y2);
+            const bool in2 = x2 >= a.cv[0] && x2 <= a.cv[1] && y2 >= a.cv[2] && y2 <= a.cv[3];
+            if (in2 == inV) continue;
+            if (CHECKED && (nb[r] & (1u << i))) continue;  // the neighbour is solid
+            const T v = inV ? -ftr[i] : ftr[i];
+            if (cx(i) != 0) acc_add(acc[4], as_acc(cx(i) > 0 ? v : -v, A()));
+            if (cy(i) != 0) acc_add(acc[5], as_acc(cy(i) > 0 ? v : -v, A()));
         }
-        int y2 = y + cy(i);
-        y2 = y2 < 0 ? y2 + a.ny : (y2 >= a.ny ? y2 - a.ny : y2);
-        const bool in2 = x2 >= a.cv[0] && x2 <= a.cv[1] && y2 >= a.cv[2] && y2 <= a.cv[3];
-        if (in2 == inV) continue;
-        if (CHECKED && (nb & (1u << i))) continue;  // the neighbour is solid
-        double v = (double)ftr[i];
-        if (DEV) v += wgt<double>(i) * a.rho0;
-        if (inV) v = -v;
-        acc[4] += cx(i) * v;
-        acc[5] += cy(i) * v;
     }
 }
 
 template <int S, bool MOMENTUM_ONLY>
-__global__ void __launch_bounds__(TILE_X * 2) k_collide_stream(StepArgs a)
+__global__ void __launch_bounds__(TILE_X *(TILE_ROWS / RowsPerThread<S>::value))
+    k_collide_stream(StepArgs a)
 {
+    constexpr int RPT = RowsPerThread<S>::value;
+    using A = typename AccOf<S>::type;
     const int tx = blockIdx.x + a.tile_off_x, ty = blockIdx.y + a.tile_off_y;
     const int x = tx * TILE_X + threadIdx.x;
     const bool checked = a.precollision || a.tile_flag[(long long)ty * a.tiles_x + tx] != 0;
     const bool cvtile = tx >= a.cvt[0] && tx <= a.cvt[1] && ty >= a.cvt[2] && ty <= a.cvt[3];
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    A acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc_zero(acc[k]);
     bool bad = false;
-    const int y0 = ty * TILE_ROWS + threadIdx.y * ROWS_PER_THREAD;
+    const int y0 = ty * TILE_ROWS + threadIdx.y * RPT;
     if (x < a.nx) {
-        if (checked) {
-#pragma unroll
-            for (int r = 0; r < ROWS_PER_THREAD; ++r)
-                if (y0 + r < a.ny) node_update<S, true, MOMENTUM_ONLY>(a, x, y0 + r, acc, cvtile, bad);
-        } else {
-#pragma unroll
-            for (int r = 0; r < ROWS_PER_THREAD; ++r)
-                if (y0 + r < a.ny) node_update<S, false, MOMENTUM_ONLY>(a, x, y0 + r, acc, cvtile, bad);
-        }
+        if (checked)
+            column_update<S, true, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
+        else
+            column_update<S, false, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
     }
     if (cvtile) {
-        block_reduce<6, TILE_X * 2>(acc);
+        block_reduce<A, 6, TILE_X *(TILE_ROWS / RPT)>(acc);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const int slot = (ty - a.cvt[2]) * (a.cvt[1] - a.cvt[0] + 1) + (tx - a.cvt[0]);
-            double *p = a.partials + CV_PARTIAL * (long long)slot;
+            A *p = (A *)a.partials + CV_PARTIAL * (long long)slot;
 #pragma unroll
-            for (int k = 0; k < CV_PARTIAL; ++k) p[k] = (MOMENTUM_ONLY && k >= 2) ? 0.0 : acc[k];
+            for (int k = 0; k < CV_PARTIAL; ++k) {
+                if (MOMENTUM_ONLY && k >= 2)
+                    acc_zero(p[k]);
+                else
+                    p[k] = acc[k];
+            }
         }
     }
     if (!MOMENTUM_ONLY) {
@@ -219,12 +327,15 @@ __global__ void __launch_bounds__(TILE_X * 2) k_collide_stream(StepArgs a)
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
                                   bool momentum_only, cudaStream_t st)
 {
-    dim3 grid(tiles_x, tiles_y), block(TILE_X, 2);
+    dim3 grid(tiles_x, tiles_y);
 #define GBLBM_CS(S)                                                                    \
-    if (momentum_only)                                                                 \
-        k_collide_stream<S, true><<<grid, block, 0, st>>>(a);                          \
-    else                                                                               \
-        k_collide_stream<S, false><<<grid, block, 0, st>>>(a);
+    {                                                                                  \
+        dim3 block(TILE_X, TILE_ROWS / RowsPerThread<S>::value);                       \
+        if (momentum_only)                                                             \
+            k_collide_stream<S, true><<<grid, block, 0, st>>>(a);                      \
+        else                                                                           \
+            k_collide_stream<S, false><<<grid, block, 0, st>>>(a);                     \
+    }
     switch (storage) {
     case LBM_F64: GBLBM_CS(LBM_F64); break;
     case LBM_F32: GBLBM_CS(LBM_F32); break;
@@ -236,26 +347,30 @@ cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, i
 }
 
 // ---------------------------------------------------------------------------
-// Link force + finalisation.  LINK_CTAS CTAs of LINK_THREADS threads share the
+// Link force + finalisation.  n_ctas CTAs of LINK_THREADS threads share the
 // links (contiguous chunks) and the control-volume partials; each writes one
-// FP64 partial row.  The last CTA to finish (atomic ticket) sums the rows in
-// slot order, so the result does not depend on which CTA finishes last, and
+// partial row.  The last CTA to finish (atomic ticket) sums the rows in slot
+// order, so the result does not depend on which CTA finishes last, and
 // completes the step's series row and the DRTT of the previous step.
 // Series row t: A(2) B(2) DRTT(2) A'(2) defect(2), where defect is the
 // collision's momentum defect inside the box, J_pre(t) - J_post(t).
+// For deviation storage the momentum of the base w_i rho0 over the links and
+// over the box-surface crossings is a fixed geometric sum (link_base,
+// flux_base, from the host) added at the end.
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
 {
     using ST = typename Traits<S>::store_t;
-    constexpr bool DEV = Traits<S>::dev;
+    using T = typename Traits<S>::comp_t;
+    using A = typename AccOf<S>::type;
     const ST *__restrict__ src = (const ST *)a.src;
     const ST *__restrict__ dst = (const ST *)a.dst;
     const long long plane = a.plane;
     // v: A(2), B(2), A'(2), J_pre(2), J_post(2), GL(2)
-    double v[LINK_PARTIAL];
+    A v[LINK_PARTIAL];
 #pragma unroll
-    for (int k = 0; k < LINK_PARTIAL; ++k) v[k] = 0.0;
+    for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(v[k]);
     const long long per = (a.nlinks + gridDim.x - 1) / gridDim.x;
     const long long k0 = per * blockIdx.x;
     const long long k1 = k0 + per < a.nlinks ? k0 + per : a.nlinks;
@@ -267,53 +382,61 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
             const int o = opp(i);
             const int x = n % a.nx, y = n / a.nx;
             const long long idx = (long long)y * a.pitch + x;
-            double fi, fo;
+            T fi, fo;
             if (a.precollision) {
-                fi = (double)to_comp(src[i * plane + idx]);
-                fo = (double)to_comp(src[o * plane + idx]);
+                fi = to_comp(src[i * plane + idx]);
+                fo = to_comp(src[o * plane + idx]);
             } else {
                 // f_i(x_f, t): pulled from x_f - c_i, or bounced when that node is solid
                 if (a.nbits[idx] & (1u << o)) {
-                    fi = (double)to_comp(src[o * plane + idx]);
+                    fi = to_comp(src[o * plane + idx]);
                 } else {
                     int sx = x - cx(i), sy = y - cy(i);
                     if (a.periodic) sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
                     sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
-                    fi = (double)to_comp(src[i * plane + (long long)sy * a.pitch + sx]);
+                    fi = to_comp(src[i * plane + (long long)sy * a.pitch + sx]);
                 }
                 // f_opp(i)(x_f, t): x_f + c_i is solid, so it is the bounced ft_i(x_f, t-1)
-                fo = (double)to_comp(src[i * plane + idx]);
+                fo = to_comp(src[i * plane + idx]);
             }
-            double ft = (double)to_comp(dst[i * plane + idx]);
-            if (DEV) {
-                const double base = wgt<double>(i) * a.rho0;  // w_i = w_opp(i)
-                fi += base;
-                fo += base;
-                ft += base;
+            const T ft = to_comp(dst[i * plane + idx]);
+            A sa, sb, sp;
+            if constexpr (S == LBM_F64) {
+                sa = fi + fo;
+                sb = 2.0 * ft;
+                sp = fi + ft;
+            } else {
+                sa = ff_two_sum(fi, fo);
+                sb = {2.0f * ft, 0.0f};
+                sp = ff_two_sum(fi, ft);
             }
-            const double ex = cx(i), ey = cy(i);
-            v[0] += ex * (fi + fo);
-            v[1] += ey * (fi + fo);
-            v[2] += 2.0 * ex * ft;
-            v[3] += 2.0 * ey * ft;
-            v[4] += ex * (fi + ft);
-            v[5] += ey * (fi + ft);
+            const int ex = cx(i), ey = cy(i);
+            if (ex != 0) {
+                acc_add(v[0], ex > 0 ? sa : -sa);
+                acc_add(v[2], ex > 0 ? sb : -sb);
+                acc_add(v[4], ex > 0 ? sp : -sp);
+            }
+            if (ey != 0) {
+                acc_add(v[1], ey > 0 ? sa : -sa);
+                acc_add(v[3], ey > 0 ? sb : -sb);
+                acc_add(v[5], ey > 0 ? sp : -sp);
+            }
         }
     }
     {
         const int per_p = (a.n_partials + gridDim.x - 1) / gridDim.x;
         const int p0 = per_p * blockIdx.x;
         const int p1 = p0 + per_p < a.n_partials ? p0 + per_p : a.n_partials;
+        const A *part = (const A *)a.partials;
         for (int s = p0 + threadIdx.x; s < p1; s += LINK_THREADS) {
-            const double *p = a.partials + CV_PARTIAL * (long long)s;
 #pragma unroll
-            for (int k = 0; k < CV_PARTIAL; ++k) v[6 + k] += p[k];
+            for (int k = 0; k < CV_PARTIAL; ++k) acc_add(v[6 + k], part[CV_PARTIAL * (long long)s + k]);
         }
     }
-    block_reduce<LINK_PARTIAL, LINK_THREADS>(v);
+    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(v);
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        double *row = a.link_partials + LINK_PARTIAL * (long long)blockIdx.x;
+        A *row = (A *)a.link_partials + LINK_PARTIAL * (long long)blockIdx.x;
 #pragma unroll
         for (int k = 0; k < LINK_PARTIAL; ++k) row[k] = v[k];
         __threadfence();
@@ -323,17 +446,27 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double w[LINK_PARTIAL];
+    A w[LINK_PARTIAL];
 #pragma unroll
-    for (int k = 0; k < LINK_PARTIAL; ++k) w[k] = 0.0;
+    for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(w[k]);
     for (int b = threadIdx.x; b < (int)gridDim.x; b += LINK_THREADS) {
-        const volatile double *row = a.link_partials + LINK_PARTIAL * (long long)b;
+        const volatile A *row = (const volatile A *)a.link_partials + LINK_PARTIAL * (long long)b;
 #pragma unroll
-        for (int k = 0; k < LINK_PARTIAL; ++k) w[k] += row[k];
+        for (int k = 0; k < LINK_PARTIAL; ++k) {
+            A r;
+            if constexpr (S == LBM_F64)
+                r = row[k];
+            else
+                r = {row[k].hi, row[k].lo};
+            acc_add(w[k], r);
+        }
     }
-    block_reduce<LINK_PARTIAL, LINK_THREADS>(w);
+    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(w);
     if (threadIdx.x == 0) {
         *a.ticket = 0u;
+        double d[LINK_PARTIAL];
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) d[k] = acc_double(w[k]);
         const long long t = *a.step_ctr;
         auto row = [&](long long s) {
             return a.series + SERIES_ROW * (a.record_series ? s : (s & 1));
@@ -342,23 +475,23 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
         // J(t-1) on the post-collision state and J(t) on the pre-collision one
         if (a.carry[4] != 0.0 && t >= 1) {
             double *q = row(t - 1);
-            q[4] = (a.carry[0] - w[6]) + a.carry[2];
-            q[5] = (a.carry[1] - w[7]) + a.carry[3];
+            q[4] = (a.carry[0] - d[6]) + a.carry[2];
+            q[5] = (a.carry[1] - d[7]) + a.carry[3];
         }
         if (!a.drtt_only) {
             double *r = row(t);
-            r[0] = w[0];
-            r[1] = w[1];
-            r[2] = w[2];
-            r[3] = w[3];
-            r[6] = w[4];
-            r[7] = w[5];
-            r[8] = w[6] - w[8];
-            r[9] = w[7] - w[9];
-            a.carry[0] = w[8];
-            a.carry[1] = w[9];
-            a.carry[2] = w[10];
-            a.carry[3] = w[11];
+            r[0] = d[0] + a.link_base[0];
+            r[1] = d[1] + a.link_base[1];
+            r[2] = d[2] + a.link_base[0];
+            r[3] = d[3] + a.link_base[1];
+            r[6] = d[4] + a.link_base[0];
+            r[7] = d[5] + a.link_base[1];
+            r[8] = d[6] - d[8];
+            r[9] = d[7] - d[9];
+            a.carry[0] = d[8];
+            a.carry[1] = d[9];
+            a.carry[2] = d[10] + a.flux_base[0];
+            a.carry[3] = d[11] + a.flux_base[1];
             a.carry[4] = 1.0;
             *a.step_ctr = t + 1;
         }
