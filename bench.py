@@ -317,7 +317,7 @@ def run_ours(a):
                        "thickness": w.thickness, "alpha_deg": w.alpha_deg, "re": w.re,
                        "tau": w.tau, "u_in": w.u_in, "storage": storage,
                        "forces_per_step": ["MEA_A", "MEA_B", "DRTT", "MEA_A_RTT"],
-                       "l2": "inputs larger than L2 (2 x %.0f MB populations)"
+                       "l2": "inputs larger than L2 (3 rotating x %.0f MB population buffers)"
                              % (9 * 4 * w.nodes / 1e6),
                        "parallelism": "replicas%d" % world},
             "roofline": {"bound": "hbm", "achieved": round(rl["achieved"], 1), "peak": peak,

@@ -18,7 +18,12 @@ namespace {
 
 thread_local std::string g_thread_err;
 
-constexpr int GRAPH_STEPS = 16;  // steps per captured graph (even: buffers return)
+// Three population buffers rotate: step t reads buffer b(t-1) and writes b(t).
+// The link kernel of step t (reading b(t-1) and b(t)) runs on a side stream,
+// concurrently with the collide-stream kernel of step t+1 (writing b(t+1));
+// the collide-stream kernel of step t+2 waits for it before overwriting b(t-1).
+constexpr int NBUF = 3;
+constexpr int GRAPH_STEPS = 15;  // steps per captured graph (a multiple of NBUF)
 constexpr int TIMING_BATCH = 64;
 
 }  // namespace
@@ -38,8 +43,11 @@ struct lbm_ctx {
     void *alloc_user = nullptr;
     size_t elem = 4;
     long long plane = 0;
-    void *pop[2] = {nullptr, nullptr};
-    int cur = 0;
+    void *pop[NBUF] = {nullptr, nullptr, nullptr};
+    int cur = 0;                 // buffer holding the latest state
+    cudaStream_t side = nullptr; // link kernels
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_read[NBUF] = {nullptr, nullptr, nullptr};
+    bool ev_live[NBUF] = {false, false, false};
     uint8_t *mask_d = nullptr;
     uint16_t *nbits = nullptr;
     uint8_t *tile_flag = nullptr;
@@ -47,7 +55,7 @@ struct lbm_ctx {
     long long nlinks = 0;
     double *u_row = nullptr;
     void *inlet = nullptr;
-    double *partials = nullptr;
+    double *partials = nullptr;  // NBUF slices, one per destination buffer
     double *link_partials = nullptr;
     unsigned int *ticket = nullptr;
     int link_ctas = 1;
@@ -61,7 +69,7 @@ struct lbm_ctx {
     int precollision = 1;
     long long carry_from = 0;    // first step of the current DRTT chain
     long long drtt_ready = 0;    // DRTT(s) is final for s < drtt_ready
-    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur][big/small]
+    cudaGraphExec_t graph[NBUF][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     bool timing = false;
     std::vector<cudaEvent_t> events;
     double kt_ms[2] = {0, 0};
@@ -230,16 +238,18 @@ bool range_ok(int lo, int hi, int n, bool whole_allowed)
     return whole_allowed && lo == 0 && hi == n - 1;
 }
 
-StepArgs step_args(lbm_ctx *h, int src, int precollision)
+int next_buf(int b) { return b + 1 == NBUF ? 0 : b + 1; }
+
+StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
 {
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.src = h->pop[src];
-    a.dst = h->pop[src ^ 1];
+    a.dst = h->pop[dst];
     a.nbits = h->nbits;
     a.tile_flag = h->tile_flag;
     a.inlet = h->inlet;
-    a.partials = h->partials;
+    a.partials = h->partials + (size_t)dst * CV_PARTIAL * h->n_cv_tiles;
     a.status = h->status;
     a.step_ctr = h->step_ctr;
     a.plane = h->plane;
@@ -253,21 +263,25 @@ StepArgs step_args(lbm_ctx *h, int src, int precollision)
     a.rho0 = h->rho0;
     a.gx = h->g[0];
     a.gy = h->g[1];
+    a.omega_f = (float)h->omega;
+    a.rho0_f = (float)h->rho0;
+    a.gx_f = (float)h->g[0];
+    a.gy_f = (float)h->g[1];
     memcpy(a.cv, h->cv, sizeof(a.cv));
     memcpy(a.cvt, h->cvt, sizeof(a.cvt));
     return a;
 }
 
-LinkArgs link_args(lbm_ctx *h, int src, int precollision, int drtt_only)
+LinkArgs link_args(lbm_ctx *h, int src, int dst, int precollision, int drtt_only)
 {
     LinkArgs a;
     memset(&a, 0, sizeof(a));
     a.src = h->pop[src];
-    a.dst = h->pop[src ^ 1];
+    a.dst = h->pop[dst];
     a.nbits = h->nbits;
     a.links = h->links;
     a.nlinks = h->nlinks;
-    a.partials = h->partials;
+    a.partials = h->partials + (size_t)dst * CV_PARTIAL * h->n_cv_tiles;
     a.n_partials = h->n_cv_tiles;
     a.link_partials = h->link_partials;
     a.ticket = h->ticket;
@@ -289,18 +303,43 @@ LinkArgs link_args(lbm_ctx *h, int src, int precollision, int drtt_only)
     return a;
 }
 
-// One step t -> t+1 from buffer src: collide-stream, then the link kernel.
+// One step t -> t+1 from buffer src into next_buf(src): the collide-stream
+// kernel on the handle's stream, then the link kernel.  Normally the link
+// kernel goes to the side stream (forked after the collide-stream kernel) and
+// the next-but-one collide-stream kernel waits for it; with timing events
+// (ev != NULL) both run in order on the handle's stream, each between events.
 cudaError_t launch_one_step(lbm_ctx *h, int src, int precollision, cudaEvent_t *ev)
 {
-    StepArgs sa = step_args(h, src, precollision);
-    if (ev) cudaEventRecord(ev[0], h->stream);
-    cudaError_t e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false, h->stream);
+    const int dst = next_buf(src);
+    cudaError_t e = cudaSuccess;
+    if (!ev && h->ev_live[dst]) e = cudaStreamWaitEvent(h->stream, h->ev_read[dst], 0);
     if (e != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[1], h->stream);
-    LinkArgs la = link_args(h, src, precollision, 0);
-    e = launch_link_force(h->storage, la, h->stream);
-    if (ev) cudaEventRecord(ev[2], h->stream);
+    StepArgs sa = step_args(h, src, dst, precollision);
+    if (ev) cudaEventRecord(ev[0], h->stream);
+    e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false, h->stream);
+    if (e != cudaSuccess) return e;
+    LinkArgs la = link_args(h, src, dst, precollision, 0);
+    if (ev) {
+        cudaEventRecord(ev[1], h->stream);
+        e = launch_link_force(h->storage, la, h->stream);
+        cudaEventRecord(ev[2], h->stream);
+    } else {
+        e = cudaEventRecord(h->ev_fork, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+        if (e == cudaSuccess) e = launch_link_force(h->storage, la, h->side);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_read[src], h->side);
+        h->ev_live[src] = true;
+    }
     h->launches += 2;
+    return e;
+}
+
+// Join the side stream back into the handle's stream.
+cudaError_t join_side(lbm_ctx *h)
+{
+    cudaError_t e = cudaEventRecord(h->ev_join, h->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    for (int b = 0; b < NBUF; ++b) h->ev_live[b] = false;
     return e;
 }
 
@@ -316,12 +355,18 @@ void drop_graphs(lbm_ctx *h)
 
 lbm_status build_graph(lbm_ctx *h, int p, int k)
 {
-    int steps = k == 0 ? GRAPH_STEPS : 2;
+    int steps = k == 0 ? GRAPH_STEPS : NBUF;
     cudaGraph_t g = nullptr;
+    for (int b = 0; b < NBUF; ++b) h->ev_live[b] = false;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t le = cudaSuccess;
     long long saved = h->launches;
-    for (int s = 0; s < steps && le == cudaSuccess; ++s) le = launch_one_step(h, p ^ (s & 1), 0, nullptr);
+    int b = p;
+    for (int s = 0; s < steps && le == cudaSuccess; ++s) {
+        le = launch_one_step(h, b, 0, nullptr);
+        b = next_buf(b);
+    }
+    if (le == cudaSuccess) le = join_side(h);
     h->launches = saved;
     cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
     if (le != cudaSuccess) {
@@ -379,13 +424,15 @@ lbm_status finalize_drtt(lbm_ctx *h)
     if (h->t < 1 || h->t - 1 < h->carry_from || h->precollision)
         return set_err(h, LBM_ESTATE, "DRTT of step %lld needs J of step %lld, which is not available",
                        h->t - 1, h->t);
-    StepArgs sa = step_args(h, h->cur, 0);
+    const int slot = next_buf(h->cur);
+    StepArgs sa = step_args(h, h->cur, slot, 0);
+    sa.dst = nullptr;  // the momentum-only pass stores nothing
     sa.tile_off_x = h->cvt[0];
     sa.tile_off_y = h->cvt[2];
     CK(h, launch_collide_stream(h->storage, sa, h->cvt[1] - h->cvt[0] + 1, h->cvt[3] - h->cvt[2] + 1,
                                 true, h->stream),
        "momentum pass");
-    LinkArgs la = link_args(h, h->cur, 0, 1);
+    LinkArgs la = link_args(h, h->cur, slot, 0, 1);
     CK(h, launch_link_force(h->storage, la, h->stream), "DRTT finalize");
     h->launches += 2;
     h->drtt_ready = h->t;
@@ -397,7 +444,11 @@ void free_all(lbm_ctx *h)
     drop_graphs(h);
     for (auto e : h->events) cudaEventDestroy(e);
     h->events.clear();
-    void *bufs[] = {h->pop[0], h->pop[1], h->mask_d, h->nbits, h->tile_flag, h->links,
+    cudaEvent_t evs[] = {h->ev_fork, h->ev_join, h->ev_read[0], h->ev_read[1], h->ev_read[2]};
+    for (auto e : evs)
+        if (e) cudaEventDestroy(e);
+    if (h->side) cudaStreamDestroy(h->side);
+    void *bufs[] = {h->pop[0], h->pop[1], h->pop[2], h->mask_d, h->nbits, h->tile_flag, h->links,
                     h->u_row, h->inlet, h->partials, h->link_partials, h->ticket, h->series,
                     h->carry, h->step_ctr, h->status};
     for (void *p : bufs) dev_free(h, p);
@@ -523,6 +574,19 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
         }
         h->own_stream = true;
     }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        for (int b = 0; b < NBUF && e == cudaSuccess; ++b)
+            e = cudaEventCreateWithFlags(&h->ev_read[b], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            g_thread_err = std::string("stream/event create: ") + cudaGetErrorString(e);
+            free_all(h);
+            delete h;
+            return LBM_ECUDA;
+        }
+    }
 
     lbm_status st = LBM_OK;
     auto fail = [&](lbm_status s) {
@@ -546,12 +610,13 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     const size_t pop_bytes = 9 * (size_t)h->plane * h->elem;
     ALLOC(h->pop[0], void *, pop_bytes);
     ALLOC(h->pop[1], void *, pop_bytes);
+    ALLOC(h->pop[2], void *, pop_bytes);
     ALLOC(h->mask_d, uint8_t *, N);
     ALLOC(h->nbits, uint16_t *, sizeof(uint16_t) * h->plane);
     ALLOC(h->tile_flag, uint8_t *, (size_t)h->tiles_x * h->tiles_y);
     ALLOC(h->u_row, double *, sizeof(double) * ny);
     ALLOC(h->inlet, void *, 9 * (size_t)ny * h->elem);
-    ALLOC(h->partials, double *, sizeof(double) * CV_PARTIAL * h->n_cv_tiles);
+    ALLOC(h->partials, double *, sizeof(double) * NBUF * CV_PARTIAL * h->n_cv_tiles);
     ALLOC(h->link_partials, double *, sizeof(double) * LINK_PARTIAL * MAX_LINK_CTAS);
     ALLOC(h->ticket, unsigned int *, sizeof(unsigned int));
     ALLOC(h->carry, double *, sizeof(double) * 8);
@@ -565,8 +630,9 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     cudaStream_t s = h->stream;
     CKC(cudaMemsetAsync(h->pop[0], 0, pop_bytes, s), "memset");
     CKC(cudaMemsetAsync(h->pop[1], 0, pop_bytes, s), "memset");
+    CKC(cudaMemsetAsync(h->pop[2], 0, pop_bytes, s), "memset");
     CKC(cudaMemsetAsync(h->nbits, 0, sizeof(uint16_t) * h->plane, s), "memset");
-    CKC(cudaMemsetAsync(h->partials, 0, sizeof(double) * CV_PARTIAL * h->n_cv_tiles, s), "memset");
+    CKC(cudaMemsetAsync(h->partials, 0, sizeof(double) * NBUF * CV_PARTIAL * h->n_cv_tiles, s), "memset");
     CKC(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s), "memset");
     CKC(cudaMemsetAsync(h->carry, 0, sizeof(double) * 8, s), "memset");
     CKC(cudaMemsetAsync(h->step_ctr, 0, sizeof(long long), s), "memset");
@@ -638,8 +704,9 @@ lbm_status lbm_step(lbm_ctx *h, int n)
             if (!e) CK(h, cudaEventCreate(&e), "event create");
     }
     int nev = 0;
+    for (int b = 0; b < NBUF; ++b) h->ev_live[b] = false;
     while (n > 0) {
-        if (h->precollision || h->timing || n < 2) {
+        if (h->precollision || h->timing || n < NBUF) {
             cudaEvent_t *ev = h->timing ? &h->events[3 * nev] : nullptr;
             CK(h, launch_one_step(h, h->cur, h->precollision, ev), "step launch");
             if (h->timing && ++nev == TIMING_BATCH) {
@@ -647,13 +714,14 @@ lbm_status lbm_step(lbm_ctx *h, int n)
                 if (st != LBM_OK) return st;
                 nev = 0;
             }
-            h->cur ^= 1;
+            h->cur = next_buf(h->cur);
             h->precollision = 0;
             h->t += 1;
             n -= 1;
         } else {
             int k = n >= GRAPH_STEPS ? 0 : 1;
-            int steps = k == 0 ? GRAPH_STEPS : 2;
+            int steps = k == 0 ? GRAPH_STEPS : NBUF;
+            CK(h, join_side(h), "join");
             if (!h->graph[h->cur][k]) {
                 st = build_graph(h, h->cur, k);
                 if (st != LBM_OK) return st;
@@ -664,6 +732,7 @@ lbm_status lbm_step(lbm_ctx *h, int n)
             n -= steps;
         }
     }
+    CK(h, join_side(h), "join");
     if (h->timing) {
         st = flush_timing(h, nev);
         if (st != LBM_OK) return st;

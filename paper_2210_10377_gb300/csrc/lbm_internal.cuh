@@ -1,7 +1,7 @@
 // lbm_internal.cuh -- declarations shared by the library's translation units.
 //
 // Layout in HBM (all device buffers owned by the handle):
-//   populations  two buffers, each 9 planes [ny][pitch] of the storage type
+//   populations  three rotating buffers, each 9 planes [ny][pitch] of the storage type
 //                (pitch = nx rounded up to 64 elements, so every row starts on a
 //                128-byte boundary for FP16 and wider types);
 //   nbits        uint16 [ny][pitch]: bit 0 = node is solid, bit i (1..8) =
@@ -12,7 +12,7 @@
 //                bounce-back path);
 //   links        int32 [L], n*8 + (i-1), ascending;
 //   inlet        [9][ny] storage-type inlet populations feq(rho0, u_in(y));
-//   partials     [n_cv_tiles][6] per-tile J(t) on the pre- and on the
+//   partials     [3][n_cv_tiles][6] (one slice per destination buffer) per-tile J(t) on the pre- and on the
 //                post-collision state, and gained-minus-lost(t); FP64 for FP64
 //                storage, float-float pairs otherwise (8 bytes either way);
 //   link_partials [n_ctas][12] per-CTA rows of the link kernel, same types;
@@ -104,6 +104,7 @@ struct StepArgs {
     int tiles_x;             // tiles per row band
     int tile_off_x, tile_off_y;  // added to blockIdx (momentum-only pass)
     double omega, rho0, gx, gy;
+    float omega_f, rho0_f, gx_f, gy_f;  // the same in FP32 (no FP64 conversions in FP32 kernels)
     int cv[4];               // inclusive control-volume box
     int cvt[4];              // inclusive tile rectangle holding the box and its halo
 };

@@ -127,6 +127,10 @@ __device__ __forceinline__ void block_reduce(A (&v)[NV])
     __syncthreads();
 }
 
+template <typename T> __device__ __forceinline__ T param(double d, float f);
+template <> __device__ __forceinline__ double param<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float param<float>(double, float f) { return f; }
+
 // Rows per thread of the 128 x TILE_ROWS collide-stream tile, per storage:
 // enough independent loads in flight per thread to cover HBM latency.
 template <int S> struct RowsPerThread {
@@ -216,7 +220,7 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
             // rho = R0 + sum f (R0 = rho0 for deviation storage, 0 otherwise);
             // feq - w R0 = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
             const T *g = f[r];
-            const T R0 = DEV ? (T)a.rho0 : T(0);
+            const T R0 = DEV ? param<T>(a.rho0, a.rho0_f) : T(0);
             const T jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
             const T jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
             const T drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
@@ -225,8 +229,8 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
             const T inv = T(1) / rho;
             const T ux = jx * inv, uy = jy * inv;
             const T usq = T(1.5) * (ux * ux + uy * uy);
-            const T om = (T)a.omega;
-            const T gx = (T)a.gx, gy = (T)a.gy;
+            const T om = param<T>(a.omega, a.omega_f);
+            const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
@@ -253,8 +257,8 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
             if (!MOMENTUM_ONLY) {
                 acc_add(acc[2], mom_x(ftr));
                 acc_add(acc[3], mom_y(ftr));
-                acc_add(acc[2], as_acc(-(T)a.gx, A()));
-                acc_add(acc[3], as_acc(-(T)a.gy, A()));
+                acc_add(acc[2], as_acc(-param<T>(a.gx, a.gx_f), A()));
+                acc_add(acc[3], as_acc(-param<T>(a.gy, a.gy_f), A()));
             }
         }
         if (MOMENTUM_ONLY) continue;
