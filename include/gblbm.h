@@ -44,7 +44,7 @@ typedef enum {
     LBM_ENOMEM = 2,    /* the allocator returned NULL */
     LBM_ECUDA = 3,     /* a CUDA call failed (no device, launch error, ...) */
     LBM_EUNSTABLE = 4, /* a step produced rho <= 0 or NaN (first step index in the message) */
-    LBM_ETIMEOUT = 5,  /* reserved for bounded device waits */
+    LBM_ETIMEOUT = 5,  /* a bounded device wait expired (the step's results are invalid) */
     LBM_ESTATE = 6     /* the request needs a state that does not exist yet */
 } lbm_status;
 
@@ -106,10 +106,13 @@ typedef struct {
     lbm_alloc_fn alloc;   /* NULL: cudaMalloc / cudaFree */
     lbm_free_fn free;
     void *alloc_user;
+    int kernel;           /* 0: staged collide-stream kernel wherever it applies
+                             (channel set-up); 1: direct-load kernel everywhere.
+                             Both give identical results. */
 } lbm_bc;
 
 /* Fill *bc with defaults: channel, FP32, rho0 = 1, no body force, default
- * control volume, record_series = 1, default stream, cudaMalloc. */
+ * control volume, record_series = 1, own stream, cudaMalloc, staged kernel. */
 void lbm_bc_default(lbm_bc *bc);
 
 /* Create a solver on an nx x ny grid.

@@ -36,7 +36,8 @@ class lbm_bc(C.Structure):
     _fields_ = [("kind", C.c_int), ("storage", C.c_int), ("rho0", C.c_double),
                 ("body_force", C.c_double * 2), ("cv", C.c_int * 4),
                 ("record_series", C.c_int), ("cuda_stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("kernel", C.c_int)]
 
 
 _lib = None
@@ -141,7 +142,7 @@ class Lattice:
 
     def __init__(self, mask, tau, u_in, *, kind=CHANNEL, storage="f32", rho0=1.0,
                  body_force=(0.0, 0.0), cv=None, record_series=True, stream=None,
-                 torch_alloc=True, device=0):
+                 torch_alloc=True, device=0, kernel="staged"):
         import torch
         L = lib()
         self.mask = np.ascontiguousarray(mask, np.uint8)
@@ -159,6 +160,7 @@ class Lattice:
             for k in range(4):
                 bc.cv[k] = int(cv[k])
         bc.record_series = int(bool(record_series))
+        bc.kernel = {"staged": 0, "direct": 1}[kernel]
         bc.cuda_stream = self.stream.cuda_stream
         self._alloc = _TorchAllocator(device) if torch_alloc else None
         if self._alloc is not None:

@@ -43,7 +43,9 @@ struct lbm_ctx {
     void *alloc_user = nullptr;
     size_t elem = 4;
     long long plane = 0;
-    void *pop[NBUF] = {nullptr, nullptr, nullptr};
+    void *pop[NBUF] = {nullptr, nullptr, nullptr};       // first element of plane 0
+    void *pop_base[NBUF] = {nullptr, nullptr, nullptr};  // allocations (with guards)
+    int use_bulk = 1, sm_count = 1;
     int cur = 0;                 // buffer holding the latest state
     cudaStream_t side = nullptr; // link kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_read[NBUF] = {nullptr, nullptr, nullptr};
@@ -269,6 +271,8 @@ StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
     a.gy_f = (float)h->g[1];
     memcpy(a.cv, h->cv, sizeof(a.cv));
     memcpy(a.cvt, h->cvt, sizeof(a.cvt));
+    a.use_bulk = h->use_bulk;
+    a.sm_count = h->sm_count;
     return a;
 }
 
@@ -448,7 +452,7 @@ void free_all(lbm_ctx *h)
     for (auto e : evs)
         if (e) cudaEventDestroy(e);
     if (h->side) cudaStreamDestroy(h->side);
-    void *bufs[] = {h->pop[0], h->pop[1], h->pop[2], h->mask_d, h->nbits, h->tile_flag, h->links,
+    void *bufs[] = {h->pop_base[0], h->pop_base[1], h->pop_base[2], h->mask_d, h->nbits, h->tile_flag, h->links,
                     h->u_row, h->inlet, h->partials, h->link_partials, h->ticket, h->series,
                     h->carry, h->step_ctr, h->status};
     for (void *p : bufs) dev_free(h, p);
@@ -496,6 +500,8 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if (n_u_in != 1 && n_u_in != ny)
         return set_err(nullptr, LBM_EINVAL, "n_u_in must be 1 or ny (got %d)", n_u_in);
     if (!finite_all(u_in, n_u_in)) return set_err(nullptr, LBM_EINVAL, "u_in is not finite");
+    if (bc.kernel != 0 && bc.kernel != 1)
+        return set_err(nullptr, LBM_EINVAL, "unknown kernel choice %d", bc.kernel);
     if (bc.kind != LBM_BC_CHANNEL && bc.kind != LBM_BC_PERIODIC)
         return set_err(nullptr, LBM_EINVAL, "unknown boundary kind %d", bc.kind);
     if (bc.storage < LBM_F64 || bc.storage > LBM_F16_DEV)
@@ -547,6 +553,15 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if (bc.storage == LBM_F32_DEV || bc.storage == LBM_F16_DEV)
         base_sums(mask, nx, ny, periodic, cv, bc.rho0, h->link_base, h->flux_base);
     h->record_series = bc.record_series ? 1 : 0;
+    h->use_bulk = bc.kernel == 0;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            h->sm_count = sms;
+        else
+            cudaGetLastError();
+    }
     h->alloc_fn = bc.alloc;
     h->free_fn = bc.free;
     h->alloc_user = bc.alloc_user;
@@ -554,14 +569,14 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     h->pitch = (nx + PITCH_ALIGN - 1) / PITCH_ALIGN * PITCH_ALIGN;
     h->plane = (long long)ny * h->pitch;
     h->tiles_x = (nx + TILE_X - 1) / TILE_X;
-    h->tiles_y = (ny + TILE_ROWS - 1) / TILE_ROWS;
+    h->tiles_y = (ny + tile_rows(h->storage) - 1) / tile_rows(h->storage);
     {
         int hx0 = cv[0] - 1 < 0 ? 0 : cv[0] - 1, hx1 = cv[1] + 1 > nx - 1 ? nx - 1 : cv[1] + 1;
         int hy0 = cv[2] - 1 < 0 ? 0 : cv[2] - 1, hy1 = cv[3] + 1 > ny - 1 ? ny - 1 : cv[3] + 1;
         h->cvt[0] = hx0 / TILE_X;
         h->cvt[1] = hx1 / TILE_X;
-        h->cvt[2] = hy0 / TILE_ROWS;
-        h->cvt[3] = hy1 / TILE_ROWS;
+        h->cvt[2] = hy0 / tile_rows(h->storage);
+        h->cvt[3] = hy1 / tile_rows(h->storage);
         h->n_cv_tiles = (h->cvt[1] - h->cvt[0] + 1) * (h->cvt[3] - h->cvt[2] + 1);
     }
     if (bc.cuda_stream) {
@@ -607,10 +622,15 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     } while (0)
 
     const size_t N = (size_t)nx * ny;
+    // The staged kernel copies whole row segments starting 16 bytes before a
+    // tile and ending past the last column; guard bytes before and after each
+    // buffer keep those copies inside the allocation (their values are never used).
     const size_t pop_bytes = 9 * (size_t)h->plane * h->elem;
-    ALLOC(h->pop[0], void *, pop_bytes);
-    ALLOC(h->pop[1], void *, pop_bytes);
-    ALLOC(h->pop[2], void *, pop_bytes);
+    const size_t guard_front = 256, guard_back = 2048;
+    for (int b = 0; b < NBUF; ++b) {
+        ALLOC(h->pop_base[b], void *, guard_front + pop_bytes + guard_back);
+        h->pop[b] = (char *)h->pop_base[b] + guard_front;
+    }
     ALLOC(h->mask_d, uint8_t *, N);
     ALLOC(h->nbits, uint16_t *, sizeof(uint16_t) * h->plane);
     ALLOC(h->tile_flag, uint8_t *, (size_t)h->tiles_x * h->tiles_y);
@@ -628,9 +648,8 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     std::vector<double> urow(ny);
     for (int y = 0; y < ny; ++y) urow[y] = n_u_in == 1 ? u_in[0] : u_in[y];
     cudaStream_t s = h->stream;
-    CKC(cudaMemsetAsync(h->pop[0], 0, pop_bytes, s), "memset");
-    CKC(cudaMemsetAsync(h->pop[1], 0, pop_bytes, s), "memset");
-    CKC(cudaMemsetAsync(h->pop[2], 0, pop_bytes, s), "memset");
+    for (int b = 0; b < NBUF; ++b)
+        CKC(cudaMemsetAsync(h->pop_base[b], 0, guard_front + pop_bytes + guard_back, s), "memset");
     CKC(cudaMemsetAsync(h->nbits, 0, sizeof(uint16_t) * h->plane, s), "memset");
     CKC(cudaMemsetAsync(h->partials, 0, sizeof(double) * NBUF * CV_PARTIAL * h->n_cv_tiles, s), "memset");
     CKC(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s), "memset");
@@ -641,7 +660,8 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     CKC(cudaMemcpyAsync(h->mask_d, mask, N, cudaMemcpyHostToDevice, s), "H2D mask");
     CKC(cudaMemcpyAsync(h->u_row, urow.data(), sizeof(double) * ny, cudaMemcpyHostToDevice, s), "H2D u_in");
     CKC(launch_node_bits(h->mask_d, h->nbits, nx, ny, h->pitch, periodic, s), "node bits");
-    CKC(launch_tile_flags(h->nbits, nx, ny, h->pitch, periodic, h->tile_flag, h->tiles_x, h->tiles_y, s),
+    CKC(launch_tile_flags(h->nbits, nx, ny, h->pitch, periodic, h->tile_flag, h->tiles_x, h->tiles_y,
+                          tile_rows(h->storage), s),
         "tile flags");
     // link list: count, scan, scatter
     const int nb = link_blocks(nx, ny);
@@ -742,6 +762,8 @@ lbm_status lbm_step(lbm_ctx *h, int n)
        "D2H status");
     CK(h, cudaStreamSynchronize(h->stream), "step sync");
     if (h->t - 1 > h->carry_from) h->drtt_ready = h->t - 1 > h->drtt_ready ? h->t - 1 : h->drtt_ready;
+    if (status[0] & 2)
+        return set_err(h, LBM_ETIMEOUT, "a bounded wait for staged copies expired");
     if (status[0]) return set_err(h, LBM_EUNSTABLE, "rho <= 0 or NaN first seen at step %d", status[1]);
     return LBM_OK;
 }

@@ -29,16 +29,22 @@
 
 namespace gblbm {
 
-// Collide-stream tile: 128 nodes along x by TILE_ROWS rows; one CTA per tile,
-// 128 threads along x, each thread walking a few rows of one column.
+// Collide-stream tiles: 128 nodes along x by tile_rows(storage) rows.
 constexpr int TILE_X = 128;
-constexpr int TILE_ROWS = 4;
+constexpr int BULK_THREADS = 512;  // staged kernel: threads per CTA
+constexpr int BULK_STAGES = 3;     // staged kernel: tiles in flight per CTA
+constexpr unsigned int WAIT_LIMIT = 1u << 22;  // bound on every mbarrier wait loop
 constexpr int PITCH_ALIGN = 64;
 constexpr int LINK_THREADS = 128;
 constexpr int MAX_LINK_CTAS = 148;
 constexpr int CV_PARTIAL = 6;
 constexpr int LINK_PARTIAL = 12;
 constexpr int SERIES_ROW = 10;
+
+__host__ __device__ constexpr int tile_rows(int storage)
+{
+    return storage == LBM_F64 ? 4 : (storage == LBM_F16_DEV ? 16 : 8);
+}
 
 // ---- D2Q9 (Section II, Table tabD2Q9) as compile-time functions ----
 __host__ __device__ constexpr int cx(int i) {
@@ -107,6 +113,8 @@ struct StepArgs {
     float omega_f, rho0_f, gx_f, gy_f;  // the same in FP32 (no FP64 conversions in FP32 kernels)
     int cv[4];               // inclusive control-volume box
     int cvt[4];              // inclusive tile rectangle holding the box and its halo
+    int use_bulk;            // staged kernel allowed (channel set-up, pulled state)
+    int sm_count;            // persistent grid size of the staged kernel
 };
 
 struct LinkArgs {
@@ -147,7 +155,8 @@ cudaError_t launch_link_scatter(const uint16_t *nbits, int nx, int ny, int pitch
                                 const int *block_off, int32_t *links, long long cap,
                                 cudaStream_t st);
 cudaError_t launch_tile_flags(const uint16_t *nbits, int nx, int ny, int pitch, int periodic,
-                              uint8_t *flags, int tiles_x, int tiles_y, cudaStream_t st);
+                              uint8_t *flags, int tiles_x, int tiles_y, int rows,
+                              cudaStream_t st);
 int link_blocks(int nx, int ny);
 
 cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *mask, int nx,

@@ -234,12 +234,12 @@ cudaError_t launch_link_scatter(const uint16_t *nbits, int nx, int ny, int pitch
 // for the tile holding the outlet too.
 // ---------------------------------------------------------------------------
 __global__ void k_tile_flags(const uint16_t *__restrict__ nbits, int nx, int ny, int pitch,
-                             int periodic, uint8_t *__restrict__ flags, int tiles_x)
+                             int periodic, uint8_t *__restrict__ flags, int tiles_x, int rows)
 {
     int x = blockIdx.x * TILE_X + threadIdx.x;
     int any = 0;
-    for (int r = 0; r < TILE_ROWS; ++r) {
-        int y = blockIdx.y * TILE_ROWS + r;
+    for (int r = 0; r < rows; ++r) {
+        int y = blockIdx.y * rows + r;
         if (x < nx && y < ny) {
             any |= nbits[(long long)y * pitch + x] != 0;
             if (!periodic && x == nx - 1) any |= nbits[(long long)y * pitch + nx - 2] != 0;
@@ -250,10 +250,11 @@ __global__ void k_tile_flags(const uint16_t *__restrict__ nbits, int nx, int ny,
 }
 
 cudaError_t launch_tile_flags(const uint16_t *nbits, int nx, int ny, int pitch, int periodic,
-                              uint8_t *flags, int tiles_x, int tiles_y, cudaStream_t st)
+                              uint8_t *flags, int tiles_x, int tiles_y, int rows,
+                              cudaStream_t st)
 {
     dim3 grid(tiles_x, tiles_y);
-    k_tile_flags<<<grid, TILE_X, 0, st>>>(nbits, nx, ny, pitch, periodic, flags, tiles_x);
+    k_tile_flags<<<grid, TILE_X, 0, st>>>(nbits, nx, ny, pitch, periodic, flags, tiles_x, rows);
     return cudaGetLastError();
 }
 

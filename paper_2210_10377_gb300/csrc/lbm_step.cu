@@ -131,21 +131,119 @@ template <typename T> __device__ __forceinline__ T param(double d, float f);
 template <> __device__ __forceinline__ double param<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float param<float>(double, float f) { return f; }
 
-// Rows per thread of the 128 x TILE_ROWS collide-stream tile, per storage:
-// enough independent loads in flight per thread to cover HBM latency.
-template <int S> struct RowsPerThread {
-    static constexpr int value = 2;
-};
-template <> struct RowsPerThread<LBM_F64> {
-    static constexpr int value = 1;
-};
-template <> struct RowsPerThread<LBM_F16_DEV> {
-    static constexpr int value = 4;
-};
+// ---------------------------------------------------------------------------
+// Per-node pieces shared by the two collide-stream kernels.
+// ---------------------------------------------------------------------------
+
+// BGK collision of one node: rho = R0 + sum f (R0 = rho0 for deviation storage,
+// 0 otherwise); feq - w R0 = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2)) (the
+// second-order equilibrium of Section II with theta0 = 1/3); ft = f +
+// (feq - f)/tau, plus 3 w_i c_i.g for a body force.  ftr receives ft rounded to
+// the storage type (the values that are stored).
+template <int S>
+__device__ __forceinline__ void collide_node(const StepArgs &a, const typename Traits<S>::comp_t (&g)[9],
+                                             typename Traits<S>::comp_t (&ftr)[9], bool &bad)
+{
+    using ST = typename Traits<S>::store_t;
+    using T = typename Traits<S>::comp_t;
+    constexpr bool DEV = Traits<S>::dev;
+    const T R0 = DEV ? param<T>(a.rho0, a.rho0_f) : T(0);
+    const T jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
+    const T jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
+    const T drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
+    const T rho = R0 + drho;
+    if (!(rho > T(0))) bad = true;
+    const T inv = T(1) / rho;
+    const T ux = jx * inv, uy = jy * inv;
+    const T usq = T(1.5) * (ux * ux + uy * uy);
+    const T om = param<T>(a.omega, a.omega_f);
+    const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
+        const T geq = wgt<T>(i) * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq));
+        T v = g[i] + om * (geq - g[i]);
+        if (i != 0) v += T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy);
+        ftr[i] = to_comp(to_store<ST>(v));
+    }
+}
+
+// Control-volume contributions of one fluid node (x, y).
+// acc[0..1]: J(t) of the box (Eq. rtt1) on the pre-collision f(t), as the
+// Appendix orders it; acc[2..3]: J(t) on the stored post-collision ft(t) less
+// the body-force momentum g.  BGK collision conserves momentum, so both are J(t)
+// in exact arithmetic; the second is the one whose streamed values make up
+// J(t+1), so it carries no rounding defect of the reduced-precision collision.
+// (Deviation storage: the base w_i rho0 carries no momentum, sum_i c_i w_i = 0.)
+// acc[4..5]: post-collision populations crossing the box surface, + entering,
+// - leaving (Eq. rtt7); for deviation storage the fixed base parts w_i rho0 are
+// added once by the link kernel.  nb: the node's neighbour bits (0 in tiles
+// without solids).
+template <int S, bool MOMENTUM_ONLY>
+__device__ __forceinline__ void cv_node(const StepArgs &a, int x, int y,
+                                        const typename Traits<S>::comp_t *f,
+                                        const typename Traits<S>::comp_t *ftr, uint16_t nb,
+                                        typename AccOf<S>::type (&acc)[6])
+{
+    using T = typename Traits<S>::comp_t;
+    using A = typename AccOf<S>::type;
+    const bool channel = !a.periodic;
+    const bool inV = x >= a.cv[0] && x <= a.cv[1] && y >= a.cv[2] && y <= a.cv[3];
+    if (inV) {
+        acc_add(acc[0], mom_x(f));
+        acc_add(acc[1], mom_y(f));
+        if (!MOMENTUM_ONLY) {
+            acc_add(acc[2], mom_x(ftr));
+            acc_add(acc[3], mom_y(ftr));
+            acc_add(acc[2], as_acc(-param<T>(a.gx, a.gx_f), A()));
+            acc_add(acc[3], as_acc(-param<T>(a.gy, a.gy_f), A()));
+        }
+    }
+    if (MOMENTUM_ONLY) return;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        int x2 = x + cx(i);
+        if (x2 < 0 || x2 >= a.nx) {
+            if (channel) continue;
+            x2 = x2 < 0 ? x2 + a.nx : x2 - a.nx;
+        }
+        int y2 = y + cy(i);
+        y2 = y2 < 0 ? y2 + a.ny : (y2 >= a.ny ? y2 - a.ny : y2);
+        const bool in2 = x2 >= a.cv[0] && x2 <= a.cv[1] && y2 >= a.cv[2] && y2 <= a.cv[3];
+        if (in2 == inV) continue;
+        if (nb & (1u << i)) continue;  // the neighbour is solid
+        const T v = inV ? -ftr[i] : ftr[i];
+        if (cx(i) != 0) acc_add(acc[4], as_acc(cx(i) > 0 ? v : -v, A()));
+        if (cy(i) != 0) acc_add(acc[5], as_acc(cy(i) > 0 ? v : -v, A()));
+    }
+}
+
+// Block-reduce the control-volume accumulators of a tile and store its slot.
+template <int S, bool MOMENTUM_ONLY, int NT>
+__device__ __forceinline__ void cv_store(const StepArgs &a, int tx, int ty,
+                                         typename AccOf<S>::type (&acc)[6])
+{
+    using A = typename AccOf<S>::type;
+    block_reduce<A, 6, NT>(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const int slot = (ty - a.cvt[2]) * (a.cvt[1] - a.cvt[0] + 1) + (tx - a.cvt[0]);
+        A *p = (A *)a.partials + CV_PARTIAL * (long long)slot;
+#pragma unroll
+        for (int k = 0; k < CV_PARTIAL; ++k) {
+            if (MOMENTUM_ONLY && k >= 2)
+                acc_zero(p[k]);
+            else
+                p[k] = acc[k];
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------
-// Fused pull-stream + bounce-back + boundary + BGK collision for the RPT rows
-// of one thread: all loads first, then collision and stores row by row.
+// Direct-load collide-stream kernel: one CTA of 128 x 4 threads per
+// 128 x TR tile, each thread walking TR/4 rows of one column; all of a thread's
+// loads are issued before its collisions.  Used for the first step after the
+// state was set (pre-collision state, no pull), for fully periodic domains,
+// and for the momentum-only pass.
 // CHECKED: the tile holds solid nodes (bounce-back tests needed).
 // ---------------------------------------------------------------------------
 template <int S, bool CHECKED, bool MOMENTUM_ONLY, int RPT>
@@ -155,8 +253,6 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
 {
     using ST = typename Traits<S>::store_t;
     using T = typename Traits<S>::comp_t;
-    using A = typename AccOf<S>::type;
-    constexpr bool DEV = Traits<S>::dev;
     const ST *__restrict__ src = (const ST *)a.src;
     ST *__restrict__ dst = (ST *)a.dst;
     const long long plane = a.plane;
@@ -217,78 +313,18 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
                 ftr[i] = to_comp(sv);
             }
         } else if (!MOMENTUM_ONLY) {
-            // rho = R0 + sum f (R0 = rho0 for deviation storage, 0 otherwise);
-            // feq - w R0 = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
-            const T *g = f[r];
-            const T R0 = DEV ? param<T>(a.rho0, a.rho0_f) : T(0);
-            const T jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
-            const T jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
-            const T drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
-            const T rho = R0 + drho;
-            if (!(rho > T(0))) bad = true;
-            const T inv = T(1) / rho;
-            const T ux = jx * inv, uy = jy * inv;
-            const T usq = T(1.5) * (ux * ux + uy * uy);
-            const T om = param<T>(a.omega, a.omega_f);
-            const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
+            collide_node<S>(a, f[r], ftr, bad);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
-                const T geq = wgt<T>(i) * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq));
-                T v = g[i] + om * (geq - g[i]);
-                if (i != 0) v += T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy);
-                const ST sv = to_store<ST>(v);
-                dst[i * plane + idx] = sv;
-                ftr[i] = to_comp(sv);
-            }
+            for (int i = 0; i < 9; ++i) dst[i * plane + idx] = to_store<ST>(ftr[i]);
         }
-        if (!cvtile) continue;
-        const bool inV = x >= a.cv[0] && x <= a.cv[1] && y >= a.cv[2] && y <= a.cv[3];
-        if (inV) {
-            // J(t) of the box (Eq. rtt1).  acc[0..1]: on the pre-collision f(t),
-            // as the Appendix orders it; acc[2..3]: on the stored post-collision
-            // ft(t) less the body-force momentum g.  BGK collision conserves
-            // momentum, so both are J(t) in exact arithmetic; the second is the
-            // one whose streamed values make up J(t+1), so it carries no rounding
-            // defect of the reduced-precision collision.  (Deviation storage: the
-            // base w_i rho0 carries no momentum, sum_i c_i w_i = 0.)
-            acc_add(acc[0], mom_x(f[r]));
-            acc_add(acc[1], mom_y(f[r]));
-            if (!MOMENTUM_ONLY) {
-                acc_add(acc[2], mom_x(ftr));
-                acc_add(acc[3], mom_y(ftr));
-                acc_add(acc[2], as_acc(-param<T>(a.gx, a.gx_f), A()));
-                acc_add(acc[3], as_acc(-param<T>(a.gy, a.gy_f), A()));
-            }
-        }
-        if (MOMENTUM_ONLY) continue;
-        // post-collision populations crossing the box surface: + entering, - leaving
-        // (deviation storage: the base parts w_i rho0 are added once by the link
-        // kernel, they do not change from step to step)
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            int x2 = x + cx(i);
-            if (x2 < 0 || x2 >= a.nx) {
-                if (channel) continue;
-                x2 = x2 < 0 ? x2 + a.nx : x2 - a.nx;
-            }
-            int y2 = y + cy(i);
-            y2 = y2 < 0 ? y2 + a.ny : (y2 >= a.ny ? y2 - a.ny : y2);
-            const bool in2 = x2 >= a.cv[0] && x2 <= a.cv[1] && y2 >= a.cv[2] && y2 <= a.cv[3];
-            if (in2 == inV) continue;
-            if (CHECKED && (nb[r] & (1u << i))) continue;  // the neighbour is solid
-            const T v = inV ? -ftr[i] : ftr[i];
-            if (cx(i) != 0) acc_add(acc[4], as_acc(cx(i) > 0 ? v : -v, A()));
-            if (cy(i) != 0) acc_add(acc[5], as_acc(cy(i) > 0 ? v : -v, A()));
-        }
+        if (cvtile) cv_node<S, MOMENTUM_ONLY>(a, x, y, f[r], ftr, nb[r], acc);
     }
 }
 
 template <int S, bool MOMENTUM_ONLY>
-__global__ void __launch_bounds__(TILE_X *(TILE_ROWS / RowsPerThread<S>::value))
-    k_collide_stream(StepArgs a)
+__global__ void __launch_bounds__(TILE_X * 4) k_collide_stream(StepArgs a)
 {
-    constexpr int RPT = RowsPerThread<S>::value;
+    constexpr int RPT = tile_rows(S) / 4;
     using A = typename AccOf<S>::type;
     const int tx = blockIdx.x + a.tile_off_x, ty = blockIdx.y + a.tile_off_y;
     const int x = tx * TILE_X + threadIdx.x;
@@ -298,27 +334,14 @@ __global__ void __launch_bounds__(TILE_X *(TILE_ROWS / RowsPerThread<S>::value))
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc_zero(acc[k]);
     bool bad = false;
-    const int y0 = ty * TILE_ROWS + threadIdx.y * RPT;
+    const int y0 = ty * tile_rows(S) + threadIdx.y * RPT;
     if (x < a.nx) {
         if (checked)
             column_update<S, true, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
         else
             column_update<S, false, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
     }
-    if (cvtile) {
-        block_reduce<A, 6, TILE_X *(TILE_ROWS / RPT)>(acc);
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const int slot = (ty - a.cvt[2]) * (a.cvt[1] - a.cvt[0] + 1) + (tx - a.cvt[0]);
-            A *p = (A *)a.partials + CV_PARTIAL * (long long)slot;
-#pragma unroll
-            for (int k = 0; k < CV_PARTIAL; ++k) {
-                if (MOMENTUM_ONLY && k >= 2)
-                    acc_zero(p[k]);
-                else
-                    p[k] = acc[k];
-            }
-        }
-    }
+    if (cvtile) cv_store<S, MOMENTUM_ONLY, TILE_X * 4>(a, tx, ty, acc);
     if (!MOMENTUM_ONLY) {
         const int any_bad = __syncthreads_or(bad);
         if (any_bad && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -328,18 +351,289 @@ __global__ void __launch_bounds__(TILE_X *(TILE_ROWS / RowsPerThread<S>::value))
     }
 }
 
+// ---------------------------------------------------------------------------
+// Staged collide-stream kernel (channel set-up, pulled state): persistent CTAs,
+// one per SM, walk the 128 x TR tiles round-robin.  For each tile the nine
+// source planes are brought into shared memory by bulk asynchronous copies
+// (cp.async.bulk, completing on an mbarrier): plane i needs rows
+// y0 - c_iy .. y0 - c_iy + TR - 1 (wrapped in y) and columns x0 - PAD ..
+// x0 + 128 + PAD - 1, PAD = 16 bytes of elements so that every copy starts
+// and ends on a 16-byte boundary.  NS stages are in flight while the CTA's
+// threads collide the current tile out of shared memory and store ft(t) with
+// vector stores.  Every mbarrier wait is bounded: on expiry the kernel flags
+// status bit 2 (reported as LBM_ETIMEOUT), waits boundedly for its copies and
+// returns.
+// ---------------------------------------------------------------------------
+namespace bulk {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t k = 0; k < WAIT_LIMIT; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace bulk
+
+template <int S> struct BulkCfg {
+    using ST = typename Traits<S>::store_t;
+    static constexpr int TR = tile_rows(S);
+    static constexpr int PAD = 16 / (int)sizeof(ST);
+    static constexpr int SEG = TILE_X + 2 * PAD;  // elements per staged row segment
+    static constexpr int VX = (S == LBM_F64) ? 1 : 2;  // adjacent nodes per thread along x
+    static constexpr int XT = TILE_X / VX;
+    static constexpr int RG = BULK_THREADS / XT;
+    static constexpr int RPT = TR / RG;
+    static constexpr int COPIES = 9 * TR;
+    static constexpr uint32_t COPY_BYTES = SEG * sizeof(ST);
+    static constexpr uint32_t STAGE_BYTES = COPIES * COPY_BYTES;
+    static constexpr size_t SMEM = (size_t)BULK_STAGES * STAGE_BYTES + 64;
+    static_assert(RPT * RG == TR, "tile rows must split over the row groups");
+    static_assert(COPY_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
+
+template <int S>
+__device__ __forceinline__ void bulk_issue(const StepArgs &a, unsigned char *stage, uint64_t *bar,
+                                           int tile)
+{
+    using C = BulkCfg<S>;
+    using ST = typename Traits<S>::store_t;
+    const int lane = threadIdx.x & 31;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int x0 = tx * TILE_X, y0 = ty * C::TR;
+    if (lane == 0) bulk::mbar_expect_tx(bar, C::STAGE_BYTES);
+    __syncwarp();
+    const ST *src = (const ST *)a.src;
+    for (int c = lane; c < C::COPIES; c += 32) {
+        const int i = c / C::TR, r = c % C::TR;
+        int sy = (y0 + r - cy(i)) % a.ny;
+        sy = sy < 0 ? sy + a.ny : sy;
+        const ST *g = src + (long long)i * a.plane + (long long)sy * a.pitch + (x0 - C::PAD);
+        bulk::copy_g2s(stage + (size_t)c * C::COPY_BYTES, g, C::COPY_BYTES, bar);
+    }
+}
+
+template <int S, bool CHECKED, bool FULL>
+__device__ __forceinline__ void bulk_tile(const StepArgs &a, const typename Traits<S>::store_t *sm,
+                                          int tx, int ty, bool cvtile,
+                                          typename AccOf<S>::type (&acc)[6], bool &bad)
+{
+    using C = BulkCfg<S>;
+    using ST = typename Traits<S>::store_t;
+    using T = typename Traits<S>::comp_t;
+    const ST *__restrict__ src = (const ST *)a.src;
+    ST *__restrict__ dst = (ST *)a.dst;
+    const int t = threadIdx.x;
+    const int xl = (t % C::XT) * C::VX;
+    const int rg = t / C::XT;
+    const int x0 = tx * TILE_X, y0 = ty * C::TR;
+#pragma unroll
+    for (int rr = 0; rr < C::RPT; ++rr) {
+        const int r = rg * C::RPT + rr;
+        const int y = y0 + r;
+        if (!FULL && y >= a.ny) continue;
+        T ft[C::VX][9];
+        bool store[C::VX];
+#pragma unroll
+        for (int v = 0; v < C::VX; ++v) {
+            const int x = x0 + xl + v;
+            store[v] = FULL || x < a.nx;
+            if (!store[v]) continue;
+            const long long idx = (long long)y * a.pitch + x;
+            const uint16_t nb = CHECKED ? a.nbits[idx] : (uint16_t)0;
+            if (nb & 1) {  // solid nodes are not updated
+                store[v] = false;
+                continue;
+            }
+            T f[9];
+            if (x == 0) {  // equilibrium inlet
+                const ST *in = (const ST *)a.inlet;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) ft[v][i] = to_comp(in[i * a.ny + y]);
+            } else {
+                // the outlet column x = nx-1 takes the populations of column nx-2
+                const int xs = x == a.nx - 1 ? x - 1 : x;
+                const uint16_t nbs = CHECKED ? (xs == x ? nb : a.nbits[idx - 1]) : (uint16_t)0;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    if (CHECKED && (nbs & (1u << opp(i))))
+                        f[i] = to_comp(src[opp(i) * a.plane + (long long)y * a.pitch + xs]);
+                    else
+                        f[i] = to_comp(sm[(i * C::TR + r) * C::SEG + (xs - x0) + C::PAD - cx(i)]);
+                }
+                collide_node<S>(a, f, ft[v], bad);
+            }
+            if (cvtile) cv_node<S, false>(a, x, y, f, ft[v], nb, acc);
+        }
+        const long long idx0 = (long long)y * a.pitch + x0 + xl;
+        if (C::VX == 2 && !CHECKED && store[0] && store[1]) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if constexpr (S == LBM_F16_DEV) {
+                    *(__half2 *)&dst[i * a.plane + idx0] =
+                        __halves2half2(to_store<ST>(ft[0][i]), to_store<ST>(ft[C::VX - 1][i]));
+                } else if constexpr (S != LBM_F64) {
+                    *(float2 *)&dst[i * a.plane + idx0] = make_float2(ft[0][i], ft[C::VX - 1][i]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < C::VX; ++v)
+                if (store[v])
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) dst[i * a.plane + idx0 + v] = to_store<ST>(ft[v][i]);
+        }
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(BULK_THREADS, 1) k_collide_stream_bulk(StepArgs a, int ntiles)
+{
+    using C = BulkCfg<S>;
+    using ST = typename Traits<S>::store_t;
+    using A = typename AccOf<S>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = (uint64_t *)(smem + (size_t)BULK_STAGES * C::STAGE_BYTES);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < BULK_STAGES; ++s) bulk::mbar_init(&bar[s], 1);
+        bulk::fence_barrier_init();
+    }
+    __syncthreads();
+    const int count = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (warp == 0)
+        for (int k = 0; k < BULK_STAGES && k < count; ++k)
+            bulk_issue<S>(a, smem + (size_t)k * C::STAGE_BYTES, &bar[k], blockIdx.x + k * gridDim.x);
+    for (int k = 0; k < count; ++k) {
+        const int s = k % BULK_STAGES;
+        const uint32_t parity = (uint32_t)(k / BULK_STAGES) & 1u;
+        // one thread waits (bounded) for the stage; the barrier hands the data
+        // and the outcome to the whole CTA, so every thread takes the same path
+        bool ok = true;
+        if (threadIdx.x == 0) ok = bulk::mbar_wait(&bar[s], parity);
+        if (__syncthreads_or(!ok)) {
+            // expired: flag it, wait (bounded) for this CTA's copies, return
+            if (threadIdx.x == 0) {
+                atomicOr(a.status, 2);
+                for (int j = k + 1; j < count && j < k + BULK_STAGES; ++j)
+                    bulk::mbar_wait(&bar[j % BULK_STAGES], (uint32_t)(j / BULK_STAGES) & 1u);
+            }
+            return;
+        }
+        const int tile = blockIdx.x + k * gridDim.x;
+        const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+        const bool checked = a.tile_flag[tile] != 0;
+        const bool full = (tx + 1) * TILE_X <= a.nx && (ty + 1) * C::TR <= a.ny;
+        const bool cvtile = tx >= a.cvt[0] && tx <= a.cvt[1] && ty >= a.cvt[2] && ty <= a.cvt[3];
+        const ST *sm = (const ST *)(smem + (size_t)s * C::STAGE_BYTES);
+        A acc[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc_zero(acc[j]);
+        bool bad = false;
+        if (checked)
+            bulk_tile<S, true, false>(a, sm, tx, ty, cvtile, acc, bad);
+        else if (full)
+            bulk_tile<S, false, true>(a, sm, tx, ty, cvtile, acc, bad);
+        else
+            bulk_tile<S, false, false>(a, sm, tx, ty, cvtile, acc, bad);
+        if (cvtile) cv_store<S, false, BULK_THREADS>(a, tx, ty, acc);
+        const int any_bad = __syncthreads_or(bad);  // also: every read of stage s is done
+        if (any_bad && threadIdx.x == 0) {
+            atomicOr(a.status, 1);
+            atomicMin(a.status + 1, (int)*a.step_ctr);
+        }
+        if (warp == 0 && k + BULK_STAGES < count) {
+            bulk::fence_proxy_async();
+            bulk_issue<S>(a, smem + (size_t)s * C::STAGE_BYTES, &bar[s],
+                          blockIdx.x + (k + BULK_STAGES) * gridDim.x);
+        }
+    }
+}
+
+template <int S>
+cudaError_t launch_bulk(const StepArgs &a, int tiles, int sms, cudaStream_t st)
+{
+    using C = BulkCfg<S>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_collide_stream_bulk<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    const int grid = tiles < sms ? tiles : sms;
+    k_collide_stream_bulk<S><<<grid, BULK_THREADS, C::SMEM, st>>>(a, tiles);
+    return cudaGetLastError();
+}
+
+bool bulk_applicable(const StepArgs &a)
+{
+    return !a.periodic && !a.precollision && a.use_bulk;
+}
+
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
                                   bool momentum_only, cudaStream_t st)
 {
-    dim3 grid(tiles_x, tiles_y);
-#define GBLBM_CS(S)                                                                    \
-    {                                                                                  \
-        dim3 block(TILE_X, TILE_ROWS / RowsPerThread<S>::value);                       \
-        if (momentum_only)                                                             \
-            k_collide_stream<S, true><<<grid, block, 0, st>>>(a);                      \
-        else                                                                           \
-            k_collide_stream<S, false><<<grid, block, 0, st>>>(a);                     \
+    if (!momentum_only && bulk_applicable(a)) {
+        const int tiles = tiles_x * tiles_y;
+        switch (storage) {
+        case LBM_F64: return launch_bulk<LBM_F64>(a, tiles, a.sm_count, st);
+        case LBM_F32: return launch_bulk<LBM_F32>(a, tiles, a.sm_count, st);
+        case LBM_F32_DEV: return launch_bulk<LBM_F32_DEV>(a, tiles, a.sm_count, st);
+        default: return launch_bulk<LBM_F16_DEV>(a, tiles, a.sm_count, st);
+        }
     }
+    dim3 grid(tiles_x, tiles_y), block(TILE_X, 4);
+#define GBLBM_CS(S)                                                    \
+    if (momentum_only)                                                 \
+        k_collide_stream<S, true><<<grid, block, 0, st>>>(a);          \
+    else                                                               \
+        k_collide_stream<S, false><<<grid, block, 0, st>>>(a);
     switch (storage) {
     case LBM_F64: GBLBM_CS(LBM_F64); break;
     case LBM_F32: GBLBM_CS(LBM_F32); break;
