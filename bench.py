@@ -43,6 +43,8 @@ def args_():
                    help="only create the solver and run warm-up + K steps (for ncu captures)")
     p.add_argument("--workload", default=None, help="workload name (profile mode)")
     p.add_argument("--storage", default=None, help="f64|f32|f32dev|f16dev (profile mode)")
+    p.add_argument("--kernel", default="direct", choices=["direct", "staged"],
+                   help="collide-stream kernel: direct loads or staged bulk copies")
     return p.parse_args()
 
 
@@ -347,10 +349,10 @@ def run_profile(a):
     w = inputs.WORKLOADS[a.workload] if a.workload else inputs.LARGE_F32
     storage = a.storage or w.storage
     torch.cuda.set_device(0)
-    lat = binding.Lattice(naca_mask_device(w), w.tau, w.u_in, storage=storage)
+    lat = binding.Lattice(naca_mask_device(w), w.tau, w.u_in, storage=storage, kernel=a.kernel)
     lat.step(a.warmup)
     ms = time_steps(torch, lat, a.steps)
-    print(json.dumps({"workload": w.name, "storage": storage, "steps": a.steps,
+    print(json.dumps({"workload": w.name, "storage": storage, "kernel": a.kernel, "steps": a.steps,
                       "MLUPS": round(w.nodes * a.steps / (ms / 1e3) / 1e6, 1),
                       "force_B": lat.force("B")}), flush=True)
     lat.close()

@@ -106,13 +106,13 @@ typedef struct {
     lbm_alloc_fn alloc;   /* NULL: cudaMalloc / cudaFree */
     lbm_free_fn free;
     void *alloc_user;
-    int kernel;           /* 0: staged collide-stream kernel wherever it applies
-                             (channel set-up); 1: direct-load kernel everywhere.
-                             Both give identical results. */
+    int kernel;           /* collide-stream kernel: 0 direct loads (default);
+                             1 staged bulk copies wherever it applies (channel
+                             set-up, pulled state).  Both give identical results. */
 } lbm_bc;
 
 /* Fill *bc with defaults: channel, FP32, rho0 = 1, no body force, default
- * control volume, record_series = 1, own stream, cudaMalloc, staged kernel. */
+ * control volume, record_series = 1, own stream, cudaMalloc, direct kernel. */
 void lbm_bc_default(lbm_bc *bc);
 
 /* Create a solver on an nx x ny grid.

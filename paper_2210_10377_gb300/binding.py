@@ -142,7 +142,7 @@ class Lattice:
 
     def __init__(self, mask, tau, u_in, *, kind=CHANNEL, storage="f32", rho0=1.0,
                  body_force=(0.0, 0.0), cv=None, record_series=True, stream=None,
-                 torch_alloc=True, device=0, kernel="staged"):
+                 torch_alloc=True, device=0, kernel="direct"):
         import torch
         L = lib()
         self.mask = np.ascontiguousarray(mask, np.uint8)
@@ -160,7 +160,7 @@ class Lattice:
             for k in range(4):
                 bc.cv[k] = int(cv[k])
         bc.record_series = int(bool(record_series))
-        bc.kernel = {"staged": 0, "direct": 1}[kernel]
+        bc.kernel = {"direct": 0, "staged": 1}[kernel]
         bc.cuda_stream = self.stream.cuda_stream
         self._alloc = _TorchAllocator(device) if torch_alloc else None
         if self._alloc is not None:

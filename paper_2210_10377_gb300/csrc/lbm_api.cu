@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "lbm_internal.cuh"
 
 using namespace gblbm;
@@ -45,7 +47,9 @@ struct lbm_ctx {
     long long plane = 0;
     void *pop[NBUF] = {nullptr, nullptr, nullptr};       // first element of plane 0
     void *pop_base[NBUF] = {nullptr, nullptr, nullptr};  // allocations (with guards)
-    int use_bulk = 1, sm_count = 1;
+    alignas(64) CUtensorMap tmap[NBUF];                  // [9][ny][pitch] views for TMA loads
+    bool tmap_ok = false;
+    int use_bulk = 0, sm_count = 1;
     int cur = 0;                 // buffer holding the latest state
     cudaStream_t side = nullptr; // link kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_read[NBUF] = {nullptr, nullptr, nullptr};
@@ -233,6 +237,46 @@ void base_sums(const uint8_t *mask, int nx, int ny, int periodic, const int *cv,
     flux_base[1] = rho0 * fb[1];
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map over one population buffer viewed as [9][ny][pitch], with the
+// staged kernel's box: 128 + 2 PAD columns (PAD = 16 bytes of elements), the
+// tile rows plus one above and one below, all nine planes.
+bool encode_tensor_map(CUtensorMap *m, int storage, void *base, int pitch, int ny)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const size_t elem = storage_bytes(storage);
+    const CUtensorMapDataType dt = storage == LBM_F64       ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : storage == LBM_F16_DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * elem, (cuuint64_t)pitch * ny * elem};
+    const cuuint32_t box[3] = {(cuuint32_t)(TILE_X + 2 * (16 / elem)),
+                               (cuuint32_t)(tile_rows(storage) + 2), 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool range_ok(int lo, int hi, int n, bool whole_allowed)
 {
     if (lo > hi) return false;
@@ -320,7 +364,8 @@ cudaError_t launch_one_step(lbm_ctx *h, int src, int precollision, cudaEvent_t *
     if (e != cudaSuccess) return e;
     StepArgs sa = step_args(h, src, dst, precollision);
     if (ev) cudaEventRecord(ev[0], h->stream);
-    e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false, h->stream);
+    e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false,
+                              h->tmap_ok ? (const void *)&h->tmap[src] : nullptr, h->stream);
     if (e != cudaSuccess) return e;
     LinkArgs la = link_args(h, src, dst, precollision, 0);
     if (ev) {
@@ -434,7 +479,7 @@ lbm_status finalize_drtt(lbm_ctx *h)
     sa.tile_off_x = h->cvt[0];
     sa.tile_off_y = h->cvt[2];
     CK(h, launch_collide_stream(h->storage, sa, h->cvt[1] - h->cvt[0] + 1, h->cvt[3] - h->cvt[2] + 1,
-                                true, h->stream),
+                                true, nullptr, h->stream),
        "momentum pass");
     LinkArgs la = link_args(h, h->cur, slot, 0, 1);
     CK(h, launch_link_force(h->storage, la, h->stream), "DRTT finalize");
@@ -553,7 +598,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if (bc.storage == LBM_F32_DEV || bc.storage == LBM_F16_DEV)
         base_sums(mask, nx, ny, periodic, cv, bc.rho0, h->link_base, h->flux_base);
     h->record_series = bc.record_series ? 1 : 0;
-    h->use_bulk = bc.kernel == 0;
+    h->use_bulk = bc.kernel == 1;
     {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -630,6 +675,13 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     for (int b = 0; b < NBUF; ++b) {
         ALLOC(h->pop_base[b], void *, guard_front + pop_bytes + guard_back);
         h->pop[b] = (char *)h->pop_base[b] + guard_front;
+    }
+    if (h->use_bulk) {
+        h->tmap_ok = true;
+        for (int b = 0; b < NBUF; ++b)
+            h->tmap_ok = h->tmap_ok && encode_tensor_map(&h->tmap[b], h->storage, h->pop[b], h->pitch, ny);
+        if (!h->tmap_ok)
+            return fail(set_err(h, LBM_ECUDA, "tensor maps for the staged kernel could not be encoded"));
     }
     ALLOC(h->mask_d, uint8_t *, N);
     ALLOC(h->nbits, uint16_t *, sizeof(uint16_t) * h->plane);

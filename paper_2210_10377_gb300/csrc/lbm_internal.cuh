@@ -21,6 +21,7 @@
 //   ticket       uint32 arrival counter of the link kernel's CTAs.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,8 +32,6 @@ namespace gblbm {
 
 // Collide-stream tiles: 128 nodes along x by tile_rows(storage) rows.
 constexpr int TILE_X = 128;
-constexpr int BULK_THREADS = 512;  // staged kernel: threads per CTA
-constexpr int BULK_STAGES = 3;     // staged kernel: tiles in flight per CTA
 constexpr unsigned int WAIT_LIMIT = 1u << 22;  // bound on every mbarrier wait loop
 constexpr int PITCH_ALIGN = 64;
 constexpr int LINK_THREADS = 128;
@@ -43,7 +42,12 @@ constexpr int SERIES_ROW = 10;
 
 __host__ __device__ constexpr int tile_rows(int storage)
 {
-    return storage == LBM_F64 ? 4 : (storage == LBM_F16_DEV ? 16 : 8);
+    return (storage == LBM_F32 || storage == LBM_F32_DEV) ? 8 : 4;
+}
+// rows per thread of the direct-load kernel (enough loads in flight per thread)
+__host__ __device__ constexpr int direct_rpt(int storage)
+{
+    return storage == LBM_F64 ? 1 : (storage == LBM_F16_DEV ? 4 : 2);
 }
 
 // ---- D2Q9 (Section II, Table tabD2Q9) as compile-time functions ----
@@ -113,7 +117,7 @@ struct StepArgs {
     float omega_f, rho0_f, gx_f, gy_f;  // the same in FP32 (no FP64 conversions in FP32 kernels)
     int cv[4];               // inclusive control-volume box
     int cvt[4];              // inclusive tile rectangle holding the box and its halo
-    int use_bulk;            // staged kernel allowed (channel set-up, pulled state)
+    int use_bulk;            // staged (TMA) kernel allowed (channel set-up, pulled state)
     int sm_count;            // persistent grid size of the staged kernel
 };
 
@@ -162,8 +166,10 @@ int link_blocks(int nx, int ny);
 cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *mask, int nx,
                         int ny, int pitch, const double *u_row, double rho0, void *inlet,
                         cudaStream_t st);
+// tmap: the tensor map over the source buffer (staged kernel), or NULL
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
-                                  bool momentum_only, cudaStream_t st);
+                                  bool momentum_only, const void *tmap, cudaStream_t st);
+size_t tma_stage_bytes(int storage);
 cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st);
 cudaError_t launch_gather(int storage, const void *pop, const uint16_t *nbits, const void *inlet,
                           long long plane, int nx, int ny, int pitch, int periodic,

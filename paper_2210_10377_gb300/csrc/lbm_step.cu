@@ -239,8 +239,8 @@ __device__ __forceinline__ void cv_store(const StepArgs &a, int tx, int ty,
 }
 
 // ---------------------------------------------------------------------------
-// Direct-load collide-stream kernel: one CTA of 128 x 4 threads per
-// 128 x TR tile, each thread walking TR/4 rows of one column; all of a thread's
+// Direct-load collide-stream kernel: one CTA of 128 x (TR/RPT) threads per
+// 128 x TR tile, each thread walking RPT rows of one column; all of a thread's
 // loads are issued before its collisions.  Used for the first step after the
 // state was set (pre-collision state, no pull), for fully periodic domains,
 // and for the momentum-only pass.
@@ -322,9 +322,9 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
 }
 
 template <int S, bool MOMENTUM_ONLY>
-__global__ void __launch_bounds__(TILE_X * 4) k_collide_stream(StepArgs a)
+__global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S))) k_collide_stream(StepArgs a)
 {
-    constexpr int RPT = tile_rows(S) / 4;
+    constexpr int RPT = direct_rpt(S);
     using A = typename AccOf<S>::type;
     const int tx = blockIdx.x + a.tile_off_x, ty = blockIdx.y + a.tile_off_y;
     const int x = tx * TILE_X + threadIdx.x;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(TILE_X * 4) k_collide_stream(StepArgs a)
         else
             column_update<S, false, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
     }
-    if (cvtile) cv_store<S, MOMENTUM_ONLY, TILE_X * 4>(a, tx, ty, acc);
+    if (cvtile) cv_store<S, MOMENTUM_ONLY, TILE_X *(tile_rows(S) / RPT)>(a, tx, ty, acc);
     if (!MOMENTUM_ONLY) {
         const int any_bad = __syncthreads_or(bad);
         if (any_bad && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -353,18 +353,19 @@ __global__ void __launch_bounds__(TILE_X * 4) k_collide_stream(StepArgs a)
 
 // ---------------------------------------------------------------------------
 // Staged collide-stream kernel (channel set-up, pulled state): persistent CTAs,
-// one per SM, walk the 128 x TR tiles round-robin.  For each tile the nine
-// source planes are brought into shared memory by bulk asynchronous copies
-// (cp.async.bulk, completing on an mbarrier): plane i needs rows
-// y0 - c_iy .. y0 - c_iy + TR - 1 (wrapped in y) and columns x0 - PAD ..
-// x0 + 128 + PAD - 1, PAD = 16 bytes of elements so that every copy starts
-// and ends on a 16-byte boundary.  NS stages are in flight while the CTA's
-// threads collide the current tile out of shared memory and store ft(t) with
-// vector stores.  Every mbarrier wait is bounded: on expiry the kernel flags
-// status bit 2 (reported as LBM_ETIMEOUT), waits boundedly for its copies and
-// returns.
+// one per SM, walk the 128 x TR tiles round-robin.  For each tile one TMA copy
+// (cp.async.bulk.tensor.3d through a tensor map over [9 planes][ny][pitch])
+// brings rows y0-1 .. y0+TR of all nine source planes, columns x0-PAD ..
+// x0+127+PAD (PAD = 16 bytes of elements, so every copy starts on a 16-byte
+// boundary), into shared memory; plane i of node row r is box row r+1-c_iy.
+// Rows outside [0, ny) are zero-filled by the copy; on the first and last tile
+// rows the threads read those wrapped rows from global memory instead.
+// NS tiles are in flight per CTA while its threads collide the current tile
+// out of shared memory and store ft(t) with vector stores.  Every mbarrier
+// wait is bounded: on expiry the kernel flags status bit 2 (LBM_ETIMEOUT),
+// waits boundedly for its copies and returns.
 // ---------------------------------------------------------------------------
-namespace bulk {
+namespace tma {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -406,159 +407,147 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
-__device__ __forceinline__ void copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+__device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                        uint64_t *bar)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
 
-}  // namespace bulk
+}  // namespace tma
 
-template <int S> struct BulkCfg {
+template <int S> struct TmaCfg {
     using ST = typename Traits<S>::store_t;
     static constexpr int TR = tile_rows(S);
+    static constexpr int BR = TR + 2;                  // box rows: y0-1 .. y0+TR
     static constexpr int PAD = 16 / (int)sizeof(ST);
-    static constexpr int SEG = TILE_X + 2 * PAD;  // elements per staged row segment
+    static constexpr int SEG = TILE_X + 2 * PAD;       // box columns
     static constexpr int VX = (S == LBM_F64) ? 1 : 2;  // adjacent nodes per thread along x
     static constexpr int XT = TILE_X / VX;
-    static constexpr int RG = BULK_THREADS / XT;
-    static constexpr int RPT = TR / RG;
-    static constexpr int COPIES = 9 * TR;
-    static constexpr uint32_t COPY_BYTES = SEG * sizeof(ST);
-    static constexpr uint32_t STAGE_BYTES = COPIES * COPY_BYTES;
-    static constexpr size_t SMEM = (size_t)BULK_STAGES * STAGE_BYTES + 64;
-    static_assert(RPT * RG == TR, "tile rows must split over the row groups");
-    static_assert(COPY_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+    static constexpr int THREADS = XT * TR;            // one tile row per thread
+    static constexpr uint32_t BOX_BYTES = 9u * BR * SEG * (uint32_t)sizeof(ST);
+    static constexpr uint32_t STAGE_BYTES = (BOX_BYTES + 127u) & ~127u;
+    static constexpr int NS = (200 * 1024) / STAGE_BYTES < 8 ? (200 * 1024) / STAGE_BYTES : 8;
+    static constexpr size_t SMEM = (size_t)NS * STAGE_BYTES + 128 + 8 * NS;
+    static_assert(NS >= 2, "at least two stages");
+    static_assert(SEG * sizeof(ST) % 16 == 0, "box rows are whole 16-byte units");
+    static_assert(THREADS <= 1024, "one tile row per thread");
 };
 
-template <int S>
-__device__ __forceinline__ void bulk_issue(const StepArgs &a, unsigned char *stage, uint64_t *bar,
-                                           int tile)
+template <int S, bool CHECKED, bool FULL, bool EDGE>
+__device__ __forceinline__ void tma_tile(const StepArgs &a, const typename Traits<S>::store_t *sm,
+                                         int tx, int ty, bool cvtile,
+                                         typename AccOf<S>::type (&acc)[6], bool &bad)
 {
-    using C = BulkCfg<S>;
-    using ST = typename Traits<S>::store_t;
-    const int lane = threadIdx.x & 31;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int x0 = tx * TILE_X, y0 = ty * C::TR;
-    if (lane == 0) bulk::mbar_expect_tx(bar, C::STAGE_BYTES);
-    __syncwarp();
-    const ST *src = (const ST *)a.src;
-    for (int c = lane; c < C::COPIES; c += 32) {
-        const int i = c / C::TR, r = c % C::TR;
-        int sy = (y0 + r - cy(i)) % a.ny;
-        sy = sy < 0 ? sy + a.ny : sy;
-        const ST *g = src + (long long)i * a.plane + (long long)sy * a.pitch + (x0 - C::PAD);
-        bulk::copy_g2s(stage + (size_t)c * C::COPY_BYTES, g, C::COPY_BYTES, bar);
-    }
-}
-
-template <int S, bool CHECKED, bool FULL>
-__device__ __forceinline__ void bulk_tile(const StepArgs &a, const typename Traits<S>::store_t *sm,
-                                          int tx, int ty, bool cvtile,
-                                          typename AccOf<S>::type (&acc)[6], bool &bad)
-{
-    using C = BulkCfg<S>;
+    using C = TmaCfg<S>;
     using ST = typename Traits<S>::store_t;
     using T = typename Traits<S>::comp_t;
     const ST *__restrict__ src = (const ST *)a.src;
     ST *__restrict__ dst = (ST *)a.dst;
     const int t = threadIdx.x;
     const int xl = (t % C::XT) * C::VX;
-    const int rg = t / C::XT;
+    const int r = t / C::XT;
     const int x0 = tx * TILE_X, y0 = ty * C::TR;
+    const int y = y0 + r;
+    if (!FULL && y >= a.ny) return;
+    T ft[C::VX][9];
+    bool store[C::VX];
 #pragma unroll
-    for (int rr = 0; rr < C::RPT; ++rr) {
-        const int r = rg * C::RPT + rr;
-        const int y = y0 + r;
-        if (!FULL && y >= a.ny) continue;
-        T ft[C::VX][9];
-        bool store[C::VX];
-#pragma unroll
-        for (int v = 0; v < C::VX; ++v) {
-            const int x = x0 + xl + v;
-            store[v] = FULL || x < a.nx;
-            if (!store[v]) continue;
-            const long long idx = (long long)y * a.pitch + x;
-            const uint16_t nb = CHECKED ? a.nbits[idx] : (uint16_t)0;
-            if (nb & 1) {  // solid nodes are not updated
-                store[v] = false;
-                continue;
-            }
-            T f[9];
-            if (x == 0) {  // equilibrium inlet
-                const ST *in = (const ST *)a.inlet;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) ft[v][i] = to_comp(in[i * a.ny + y]);
-            } else {
-                // the outlet column x = nx-1 takes the populations of column nx-2
-                const int xs = x == a.nx - 1 ? x - 1 : x;
-                const uint16_t nbs = CHECKED ? (xs == x ? nb : a.nbits[idx - 1]) : (uint16_t)0;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    if (CHECKED && (nbs & (1u << opp(i))))
-                        f[i] = to_comp(src[opp(i) * a.plane + (long long)y * a.pitch + xs]);
-                    else
-                        f[i] = to_comp(sm[(i * C::TR + r) * C::SEG + (xs - x0) + C::PAD - cx(i)]);
-                }
-                collide_node<S>(a, f, ft[v], bad);
-            }
-            if (cvtile) cv_node<S, false>(a, x, y, f, ft[v], nb, acc);
+    for (int v = 0; v < C::VX; ++v) {
+        const int x = x0 + xl + v;
+        store[v] = FULL || x < a.nx;
+        if (!store[v]) continue;
+        const long long idx = (long long)y * a.pitch + x;
+        const uint16_t nb = CHECKED ? a.nbits[idx] : (uint16_t)0;
+        if (nb & 1) {  // solid nodes are not updated
+            store[v] = false;
+            continue;
         }
-        const long long idx0 = (long long)y * a.pitch + x0 + xl;
-        if (C::VX == 2 && !CHECKED && store[0] && store[1]) {
+        T f[9];
+        if (x == 0) {  // equilibrium inlet
+            const ST *in = (const ST *)a.inlet;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) ft[v][i] = to_comp(in[i * a.ny + y]);
+        } else {
+            // the outlet column x = nx-1 takes the populations of column nx-2
+            const int xs = x == a.nx - 1 ? x - 1 : x;
+            const uint16_t nbs = CHECKED ? (xs == x ? nb : a.nbits[idx - 1]) : (uint16_t)0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                if constexpr (S == LBM_F16_DEV) {
-                    *(__half2 *)&dst[i * a.plane + idx0] =
-                        __halves2half2(to_store<ST>(ft[0][i]), to_store<ST>(ft[C::VX - 1][i]));
-                } else if constexpr (S != LBM_F64) {
-                    *(float2 *)&dst[i * a.plane + idx0] = make_float2(ft[0][i], ft[C::VX - 1][i]);
+                const int sy = y - cy(i);
+                if (CHECKED && (nbs & (1u << opp(i)))) {
+                    f[i] = to_comp(src[opp(i) * a.plane + (long long)y * a.pitch + xs]);
+                } else if (EDGE && (sy < 0 || sy >= a.ny)) {
+                    const int wy = sy < 0 ? sy + a.ny : sy - a.ny;
+                    f[i] = to_comp(src[i * a.plane + (long long)wy * a.pitch + xs - cx(i)]);
+                } else {
+                    f[i] = to_comp(sm[(i * C::BR + r + 1 - cy(i)) * C::SEG + (xs - x0) + C::PAD - cx(i)]);
                 }
             }
-        } else {
-#pragma unroll
-            for (int v = 0; v < C::VX; ++v)
-                if (store[v])
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) dst[i * a.plane + idx0 + v] = to_store<ST>(ft[v][i]);
+            collide_node<S>(a, f, ft[v], bad);
         }
+        if (cvtile) cv_node<S, false>(a, x, y, f, ft[v], nb, acc);
+    }
+    const long long idx0 = (long long)y * a.pitch + x0 + xl;
+    if (C::VX == 2 && !CHECKED && store[0] && store[C::VX - 1]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if constexpr (S == LBM_F16_DEV) {
+                *(__half2 *)&dst[i * a.plane + idx0] =
+                    __halves2half2(to_store<ST>(ft[0][i]), to_store<ST>(ft[C::VX - 1][i]));
+            } else if constexpr (S != LBM_F64) {
+                *(float2 *)&dst[i * a.plane + idx0] = make_float2(ft[0][i], ft[C::VX - 1][i]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < C::VX; ++v)
+            if (store[v])
+#pragma unroll
+                for (int i = 0; i < 9; ++i) dst[i * a.plane + idx0 + v] = to_store<ST>(ft[v][i]);
     }
 }
 
 template <int S>
-__global__ void __launch_bounds__(BULK_THREADS, 1) k_collide_stream_bulk(StepArgs a, int ntiles)
+__global__ void __launch_bounds__(TmaCfg<S>::THREADS, 1)
+    k_collide_stream_tma(const StepArgs a, int ntiles, const __grid_constant__ CUtensorMap map)
 {
-    using C = BulkCfg<S>;
+    using C = TmaCfg<S>;
     using ST = typename Traits<S>::store_t;
     using A = typename AccOf<S>::type;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = (uint64_t *)(smem + (size_t)BULK_STAGES * C::STAGE_BYTES);
-    const int warp = threadIdx.x >> 5;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    uint64_t *bar = (uint64_t *)(smem + (size_t)C::NS * C::STAGE_BYTES);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < BULK_STAGES; ++s) bulk::mbar_init(&bar[s], 1);
-        bulk::fence_barrier_init();
+        for (int s = 0; s < C::NS; ++s) tma::mbar_init(&bar[s], 1);
+        tma::fence_barrier_init();
     }
     __syncthreads();
     const int count = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    if (warp == 0)
-        for (int k = 0; k < BULK_STAGES && k < count; ++k)
-            bulk_issue<S>(a, smem + (size_t)k * C::STAGE_BYTES, &bar[k], blockIdx.x + k * gridDim.x);
+    auto issue = [&](int k, int s) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+        tma::mbar_expect_tx(&bar[s], C::BOX_BYTES);
+        tma::load_3d(smem + (size_t)s * C::STAGE_BYTES, &map, tx * TILE_X - C::PAD, ty * C::TR - 1, 0,
+                     &bar[s]);
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < C::NS && k < count; ++k) issue(k, k);
     for (int k = 0; k < count; ++k) {
-        const int s = k % BULK_STAGES;
-        const uint32_t parity = (uint32_t)(k / BULK_STAGES) & 1u;
+        const int s = k % C::NS;
+        const uint32_t parity = (uint32_t)(k / C::NS) & 1u;
         // one thread waits (bounded) for the stage; the barrier hands the data
         // and the outcome to the whole CTA, so every thread takes the same path
         bool ok = true;
-        if (threadIdx.x == 0) ok = bulk::mbar_wait(&bar[s], parity);
+        if (threadIdx.x == 0) ok = tma::mbar_wait(&bar[s], parity);
         if (__syncthreads_or(!ok)) {
-            // expired: flag it, wait (bounded) for this CTA's copies, return
             if (threadIdx.x == 0) {
                 atomicOr(a.status, 2);
-                for (int j = k + 1; j < count && j < k + BULK_STAGES; ++j)
-                    bulk::mbar_wait(&bar[j % BULK_STAGES], (uint32_t)(j / BULK_STAGES) & 1u);
+                for (int j = k + 1; j < count && j < k + C::NS; ++j)
+                    tma::mbar_wait(&bar[j % C::NS], (uint32_t)(j / C::NS) & 1u);
             }
             return;
         }
@@ -566,69 +555,72 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) k_collide_stream_bulk(StepArg
         const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         const bool checked = a.tile_flag[tile] != 0;
         const bool full = (tx + 1) * TILE_X <= a.nx && (ty + 1) * C::TR <= a.ny;
+        const bool edge = ty == 0 || (ty + 1) * C::TR >= a.ny;
         const bool cvtile = tx >= a.cvt[0] && tx <= a.cvt[1] && ty >= a.cvt[2] && ty <= a.cvt[3];
         const ST *sm = (const ST *)(smem + (size_t)s * C::STAGE_BYTES);
         A acc[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) acc_zero(acc[j]);
         bool bad = false;
-        if (checked)
-            bulk_tile<S, true, false>(a, sm, tx, ty, cvtile, acc, bad);
-        else if (full)
-            bulk_tile<S, false, true>(a, sm, tx, ty, cvtile, acc, bad);
+        if (checked || edge || !full)
+            tma_tile<S, true, false, true>(a, sm, tx, ty, cvtile, acc, bad);
         else
-            bulk_tile<S, false, false>(a, sm, tx, ty, cvtile, acc, bad);
-        if (cvtile) cv_store<S, false, BULK_THREADS>(a, tx, ty, acc);
+            tma_tile<S, false, true, false>(a, sm, tx, ty, cvtile, acc, bad);
+        if (cvtile) cv_store<S, false, C::THREADS>(a, tx, ty, acc);
         const int any_bad = __syncthreads_or(bad);  // also: every read of stage s is done
         if (any_bad && threadIdx.x == 0) {
             atomicOr(a.status, 1);
             atomicMin(a.status + 1, (int)*a.step_ctr);
         }
-        if (warp == 0 && k + BULK_STAGES < count) {
-            bulk::fence_proxy_async();
-            bulk_issue<S>(a, smem + (size_t)s * C::STAGE_BYTES, &bar[s],
-                          blockIdx.x + (k + BULK_STAGES) * gridDim.x);
+        if (threadIdx.x == 0 && k + C::NS < count) {
+            tma::fence_proxy_async();
+            issue(k + C::NS, s);
         }
     }
 }
 
 template <int S>
-cudaError_t launch_bulk(const StepArgs &a, int tiles, int sms, cudaStream_t st)
+cudaError_t launch_tma(const StepArgs &a, int tiles, int sms, const void *map, cudaStream_t st)
 {
-    using C = BulkCfg<S>;
+    using C = TmaCfg<S>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_collide_stream_bulk<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_collide_stream_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::SMEM);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     const int grid = tiles < sms ? tiles : sms;
-    k_collide_stream_bulk<S><<<grid, BULK_THREADS, C::SMEM, st>>>(a, tiles);
+    k_collide_stream_tma<S><<<grid, C::THREADS, C::SMEM, st>>>(a, tiles, *(const CUtensorMap *)map);
     return cudaGetLastError();
 }
 
-bool bulk_applicable(const StepArgs &a)
+size_t tma_stage_bytes(int storage)
 {
-    return !a.periodic && !a.precollision && a.use_bulk;
+    switch (storage) {
+    case LBM_F64: return TmaCfg<LBM_F64>::STAGE_BYTES;
+    case LBM_F32: return TmaCfg<LBM_F32>::STAGE_BYTES;
+    case LBM_F32_DEV: return TmaCfg<LBM_F32_DEV>::STAGE_BYTES;
+    default: return TmaCfg<LBM_F16_DEV>::STAGE_BYTES;
+    }
 }
 
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
-                                  bool momentum_only, cudaStream_t st)
+                                  bool momentum_only, const void *tmap, cudaStream_t st)
 {
-    if (!momentum_only && bulk_applicable(a)) {
+    if (!momentum_only && !a.periodic && !a.precollision && a.use_bulk && tmap) {
         const int tiles = tiles_x * tiles_y;
         switch (storage) {
-        case LBM_F64: return launch_bulk<LBM_F64>(a, tiles, a.sm_count, st);
-        case LBM_F32: return launch_bulk<LBM_F32>(a, tiles, a.sm_count, st);
-        case LBM_F32_DEV: return launch_bulk<LBM_F32_DEV>(a, tiles, a.sm_count, st);
-        default: return launch_bulk<LBM_F16_DEV>(a, tiles, a.sm_count, st);
+        case LBM_F64: return launch_tma<LBM_F64>(a, tiles, a.sm_count, tmap, st);
+        case LBM_F32: return launch_tma<LBM_F32>(a, tiles, a.sm_count, tmap, st);
+        case LBM_F32_DEV: return launch_tma<LBM_F32_DEV>(a, tiles, a.sm_count, tmap, st);
+        default: return launch_tma<LBM_F16_DEV>(a, tiles, a.sm_count, tmap, st);
         }
     }
-    dim3 grid(tiles_x, tiles_y), block(TILE_X, 4);
+    dim3 grid(tiles_x, tiles_y), block(TILE_X, tile_rows(storage) / direct_rpt(storage));
 #define GBLBM_CS(S)                                                    \
     if (momentum_only)                                                 \
         k_collide_stream<S, true><<<grid, block, 0, st>>>(a);          \
