@@ -321,6 +321,50 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
     }
 }
 
+// Interior tiles (no solid node in or next to the tile, no wrap in y, channel
+// set-up, pulled state): every load of a thread is its own base address plus a
+// warp-uniform offset i*plane - c_iy*pitch - c_ix, every store its own base plus
+// i*plane, so the address arithmetic stays out of the per-node work.
+template <int S, bool MOMENTUM_ONLY, int RPT>
+__device__ __forceinline__ void column_update_interior(const StepArgs &a, int x, int y0,
+                                                       typename AccOf<S>::type (&acc)[6],
+                                                       bool cvtile, bool &bad)
+{
+    using ST = typename Traits<S>::store_t;
+    using T = typename Traits<S>::comp_t;
+    const long long pitch = a.pitch, plane = a.plane;
+    const bool inlet = x == 0;
+    if (inlet && MOMENTUM_ONLY) return;
+    // the outlet column x = nx-1 takes the populations of column nx-2
+    const int xs = x == a.nx - 1 ? x - 1 : x;
+    const ST *__restrict__ b = (const ST *)a.src + (long long)y0 * pitch + xs;
+    ST *__restrict__ o = (ST *)a.dst + (long long)y0 * pitch + x;
+    T f[RPT][9];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[r][i] = to_comp(b[r * pitch + i * plane - cy(i) * pitch - cx(i)]);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        T ftr[9];
+        if (inlet) {
+            const ST *in = (const ST *)a.inlet;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const ST sv = in[i * a.ny + y0 + r];
+                o[r * pitch + i * plane] = sv;
+                ftr[i] = to_comp(sv);
+            }
+        } else if (!MOMENTUM_ONLY) {
+            collide_node<S>(a, f[r], ftr, bad);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) o[r * pitch + i * plane] = to_store<ST>(ftr[i]);
+        }
+        if (cvtile) cv_node<S, MOMENTUM_ONLY>(a, x, y0 + r, f[r], ftr, 0, acc);
+    }
+}
+
 template <int S, bool MOMENTUM_ONLY>
 __global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S))) k_collide_stream(StepArgs a)
 {
@@ -335,8 +379,11 @@ __global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S))) k_coll
     for (int k = 0; k < 6; ++k) acc_zero(acc[k]);
     bool bad = false;
     const int y0 = ty * tile_rows(S) + threadIdx.y * RPT;
+    const bool interior = !checked && !a.periodic && ty > 0 && (ty + 1) * tile_rows(S) < a.ny;
     if (x < a.nx) {
-        if (checked)
+        if (interior)
+            column_update_interior<S, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
+        else if (checked)
             column_update<S, true, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
         else
             column_update<S, false, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
@@ -620,7 +667,8 @@ cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, i
         default: return launch_tma<LBM_F16_DEV>(a, tiles, a.sm_count, tmap, st);
         }
     }
-    dim3 grid(tiles_x, tiles_y), block(TILE_X, tile_rows(storage) / direct_rpt(storage));
+    dim3 grid(tiles_x, tiles_y);
+    dim3 block(TILE_X, tile_rows(storage) / direct_rpt(storage));
 #define GBLBM_CS(S)                                                    \
     if (momentum_only)                                                 \
         k_collide_stream<S, true><<<grid, block, 0, st>>>(a);          \
