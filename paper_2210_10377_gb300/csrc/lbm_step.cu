@@ -136,11 +136,17 @@ template <> __device__ __forceinline__ float param<float>(double, float f) { ret
 // ---------------------------------------------------------------------------
 
 // BGK collision of one node: rho = R0 + sum f (R0 = rho0 for deviation storage,
-// 0 otherwise); feq - w R0 = w (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2)) (the
-// second-order equilibrium of Section II with theta0 = 1/3); ft = f +
-// (feq - f)/tau, plus 3 w_i c_i.g for a body force.  ftr receives ft rounded to
-// the storage type (the values that are stored).
-template <int S>
+// 0 otherwise), u = (sum c f)/rho, and with theta0 = 1/3 the second-order
+// equilibrium of Section II, less the base w_i R0,
+//   feq_i - w_i R0 = w_i (drho + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u^2)),
+// evaluated for opposite directions together: they share the even part
+// s = drho - 1.5 rho u^2 + 4.5 rho (c.u)^2 and differ in the sign of the odd
+// part 3 rho c.u.  ft = f + (feq - f)/tau, plus 3 w_i c_i.g with a body force.
+// ftr receives ft rounded to the storage type (the values that are stored).
+__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
+
+template <int S, bool FORCE>
 __device__ __forceinline__ void collide_node(const StepArgs &a, const typename Traits<S>::comp_t (&g)[9],
                                              typename Traits<S>::comp_t (&ftr)[9], bool &bad)
 {
@@ -153,19 +159,43 @@ __device__ __forceinline__ void collide_node(const StepArgs &a, const typename T
     const T drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
     const T rho = R0 + drho;
     if (!(rho > T(0))) bad = true;
-    const T inv = T(1) / rho;
+    const T inv = recip(rho);
     const T ux = jx * inv, uy = jy * inv;
-    const T usq = T(1.5) * (ux * ux + uy * uy);
+    const T base = drho - rho * (T(1.5) * (ux * ux + uy * uy));
+    const T r45 = T(4.5) * rho, r3 = T(3) * rho;
     const T om = param<T>(a.omega, a.omega_f);
-    const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
-        const T geq = wgt<T>(i) * (drho + rho * (cu * (T(3) + T(4.5) * cu) - usq));
-        T v = g[i] + om * (geq - g[i]);
-        if (i != 0) v += T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy);
-        ftr[i] = to_comp(to_store<ST>(v));
+    const T w0 = wgt<T>(0), w1 = wgt<T>(1), w5 = wgt<T>(5);
+    T v[9];
+    v[0] = g[0] + om * (w0 * base - g[0]);
+    {  // directions 1 (+x) and 3 (-x): c.u = ux
+        const T se = base + r45 * ux * ux, so = r3 * ux;
+        v[1] = g[1] + om * (w1 * (se + so) - g[1]);
+        v[3] = g[3] + om * (w1 * (se - so) - g[3]);
     }
+    {  // directions 2 (+y) and 4 (-y): c.u = uy
+        const T se = base + r45 * uy * uy, so = r3 * uy;
+        v[2] = g[2] + om * (w1 * (se + so) - g[2]);
+        v[4] = g[4] + om * (w1 * (se - so) - g[4]);
+    }
+    {  // directions 5 (+x+y) and 7 (-x-y): c.u = ux + uy
+        const T c = ux + uy;
+        const T se = base + r45 * c * c, so = r3 * c;
+        v[5] = g[5] + om * (w5 * (se + so) - g[5]);
+        v[7] = g[7] + om * (w5 * (se - so) - g[7]);
+    }
+    {  // directions 6 (-x+y) and 8 (+x-y): c.u = uy - ux
+        const T c = uy - ux;
+        const T se = base + r45 * c * c, so = r3 * c;
+        v[6] = g[6] + om * (w5 * (se + so) - g[6]);
+        v[8] = g[8] + om * (w5 * (se - so) - g[8]);
+    }
+    if (FORCE) {
+        const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) v[i] += T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ftr[i] = to_comp(to_store<ST>(v[i]));
 }
 
 // Control-volume contributions of one fluid node (x, y).
@@ -179,7 +209,7 @@ __device__ __forceinline__ void collide_node(const StepArgs &a, const typename T
 // - leaving (Eq. rtt7); for deviation storage the fixed base parts w_i rho0 are
 // added once by the link kernel.  nb: the node's neighbour bits (0 in tiles
 // without solids).
-template <int S, bool MOMENTUM_ONLY>
+template <int S, bool MOMENTUM_ONLY, bool FORCE = false>
 __device__ __forceinline__ void cv_node(const StepArgs &a, int x, int y,
                                         const typename Traits<S>::comp_t *f,
                                         const typename Traits<S>::comp_t *ftr, uint16_t nb,
@@ -195,8 +225,10 @@ __device__ __forceinline__ void cv_node(const StepArgs &a, int x, int y,
         if (!MOMENTUM_ONLY) {
             acc_add(acc[2], mom_x(ftr));
             acc_add(acc[3], mom_y(ftr));
-            acc_add(acc[2], as_acc(-param<T>(a.gx, a.gx_f), A()));
-            acc_add(acc[3], as_acc(-param<T>(a.gy, a.gy_f), A()));
+            if (FORCE) {
+                acc_add(acc[2], as_acc(-param<T>(a.gx, a.gx_f), A()));
+                acc_add(acc[3], as_acc(-param<T>(a.gy, a.gy_f), A()));
+            }
         }
     }
     if (MOMENTUM_ONLY) return;
@@ -246,7 +278,7 @@ __device__ __forceinline__ void cv_store(const StepArgs &a, int tx, int ty,
 // and for the momentum-only pass.
 // CHECKED: the tile holds solid nodes (bounce-back tests needed).
 // ---------------------------------------------------------------------------
-template <int S, bool CHECKED, bool MOMENTUM_ONLY, int RPT>
+template <int S, bool CHECKED, bool MOMENTUM_ONLY, int RPT, bool FORCE>
 __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
                                               typename AccOf<S>::type (&acc)[6], bool cvtile,
                                               bool &bad)
@@ -313,11 +345,11 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
                 ftr[i] = to_comp(sv);
             }
         } else if (!MOMENTUM_ONLY) {
-            collide_node<S>(a, f[r], ftr, bad);
+            collide_node<S, FORCE>(a, f[r], ftr, bad);
 #pragma unroll
             for (int i = 0; i < 9; ++i) dst[i * plane + idx] = to_store<ST>(ftr[i]);
         }
-        if (cvtile) cv_node<S, MOMENTUM_ONLY>(a, x, y, f[r], ftr, nb[r], acc);
+        if (cvtile) cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y, f[r], ftr, nb[r], acc);
     }
 }
 
@@ -325,7 +357,7 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
 // set-up, pulled state): every load of a thread is its own base address plus a
 // warp-uniform offset i*plane - c_iy*pitch - c_ix, every store its own base plus
 // i*plane, so the address arithmetic stays out of the per-node work.
-template <int S, bool MOMENTUM_ONLY, int RPT>
+template <int S, bool MOMENTUM_ONLY, int RPT, bool FORCE>
 __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x, int y0,
                                                        typename AccOf<S>::type (&acc)[6],
                                                        bool cvtile, bool &bad)
@@ -357,15 +389,15 @@ __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x,
                 ftr[i] = to_comp(sv);
             }
         } else if (!MOMENTUM_ONLY) {
-            collide_node<S>(a, f[r], ftr, bad);
+            collide_node<S, FORCE>(a, f[r], ftr, bad);
 #pragma unroll
             for (int i = 0; i < 9; ++i) o[r * pitch + i * plane] = to_store<ST>(ftr[i]);
         }
-        if (cvtile) cv_node<S, MOMENTUM_ONLY>(a, x, y0 + r, f[r], ftr, 0, acc);
+        if (cvtile) cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r, f[r], ftr, 0, acc);
     }
 }
 
-template <int S, bool MOMENTUM_ONLY>
+template <int S, bool MOMENTUM_ONLY, bool FORCE>
 __global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S))) k_collide_stream(StepArgs a)
 {
     constexpr int RPT = direct_rpt(S);
@@ -382,11 +414,11 @@ __global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S))) k_coll
     const bool interior = !checked && !a.periodic && ty > 0 && (ty + 1) * tile_rows(S) < a.ny;
     if (x < a.nx) {
         if (interior)
-            column_update_interior<S, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
+            column_update_interior<S, MOMENTUM_ONLY, RPT, FORCE>(a, x, y0, acc, cvtile, bad);
         else if (checked)
-            column_update<S, true, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
+            column_update<S, true, MOMENTUM_ONLY, RPT, FORCE>(a, x, y0, acc, cvtile, bad);
         else
-            column_update<S, false, MOMENTUM_ONLY, RPT>(a, x, y0, acc, cvtile, bad);
+            column_update<S, false, MOMENTUM_ONLY, RPT, FORCE>(a, x, y0, acc, cvtile, bad);
     }
     if (cvtile) cv_store<S, MOMENTUM_ONLY, TILE_X *(tile_rows(S) / RPT)>(a, tx, ty, acc);
     if (!MOMENTUM_ONLY) {
@@ -484,7 +516,7 @@ template <int S> struct TmaCfg {
     static_assert(THREADS <= 1024, "one tile row per thread");
 };
 
-template <int S, bool CHECKED, bool FULL, bool EDGE>
+template <int S, bool CHECKED, bool FULL, bool EDGE, bool FORCE>
 __device__ __forceinline__ void tma_tile(const StepArgs &a, const typename Traits<S>::store_t *sm,
                                          int tx, int ty, bool cvtile,
                                          typename AccOf<S>::type (&acc)[6], bool &bad)
@@ -534,9 +566,9 @@ __device__ __forceinline__ void tma_tile(const StepArgs &a, const typename Trait
                     f[i] = to_comp(sm[(i * C::BR + r + 1 - cy(i)) * C::SEG + (xs - x0) + C::PAD - cx(i)]);
                 }
             }
-            collide_node<S>(a, f, ft[v], bad);
+            collide_node<S, FORCE>(a, f, ft[v], bad);
         }
-        if (cvtile) cv_node<S, false>(a, x, y, f, ft[v], nb, acc);
+        if (cvtile) cv_node<S, false, FORCE>(a, x, y, f, ft[v], nb, acc);
     }
     const long long idx0 = (long long)y * a.pitch + x0 + xl;
     if (C::VX == 2 && !CHECKED && store[0] && store[C::VX - 1]) {
@@ -558,7 +590,7 @@ __device__ __forceinline__ void tma_tile(const StepArgs &a, const typename Trait
     }
 }
 
-template <int S>
+template <int S, bool FORCE>
 __global__ void __launch_bounds__(TmaCfg<S>::THREADS, 1)
     k_collide_stream_tma(const StepArgs a, int ntiles, const __grid_constant__ CUtensorMap map)
 {
@@ -610,9 +642,9 @@ __global__ void __launch_bounds__(TmaCfg<S>::THREADS, 1)
         for (int j = 0; j < 6; ++j) acc_zero(acc[j]);
         bool bad = false;
         if (checked || edge || !full)
-            tma_tile<S, true, false, true>(a, sm, tx, ty, cvtile, acc, bad);
+            tma_tile<S, true, false, true, FORCE>(a, sm, tx, ty, cvtile, acc, bad);
         else
-            tma_tile<S, false, true, false>(a, sm, tx, ty, cvtile, acc, bad);
+            tma_tile<S, false, true, false, FORCE>(a, sm, tx, ty, cvtile, acc, bad);
         if (cvtile) cv_store<S, false, C::THREADS>(a, tx, ty, acc);
         const int any_bad = __syncthreads_or(bad);  // also: every read of stage s is done
         if (any_bad && threadIdx.x == 0) {
@@ -626,8 +658,8 @@ __global__ void __launch_bounds__(TmaCfg<S>::THREADS, 1)
     }
 }
 
-template <int S>
-cudaError_t launch_tma(const StepArgs &a, int tiles, int sms, const void *map, cudaStream_t st)
+template <int S, bool FORCE>
+cudaError_t launch_tma_f(const StepArgs &a, int tiles, int sms, const void *map, cudaStream_t st)
 {
     using C = TmaCfg<S>;
     static bool attr_set[64] = {};
@@ -635,14 +667,21 @@ cudaError_t launch_tma(const StepArgs &a, int tiles, int sms, const void *map, c
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_collide_stream_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C::SMEM);
+        e = cudaFuncSetAttribute(k_collide_stream_tma<S, FORCE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     const int grid = tiles < sms ? tiles : sms;
-    k_collide_stream_tma<S><<<grid, C::THREADS, C::SMEM, st>>>(a, tiles, *(const CUtensorMap *)map);
+    k_collide_stream_tma<S, FORCE><<<grid, C::THREADS, C::SMEM, st>>>(a, tiles, *(const CUtensorMap *)map);
     return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_tma(const StepArgs &a, int tiles, int sms, const void *map, cudaStream_t st)
+{
+    if (a.gx != 0.0 || a.gy != 0.0) return launch_tma_f<S, true>(a, tiles, sms, map, st);
+    return launch_tma_f<S, false>(a, tiles, sms, map, st);
 }
 
 size_t tma_stage_bytes(int storage)
@@ -669,11 +708,14 @@ cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, i
     }
     dim3 grid(tiles_x, tiles_y);
     dim3 block(TILE_X, tile_rows(storage) / direct_rpt(storage));
+    const bool force = a.gx != 0.0 || a.gy != 0.0;
 #define GBLBM_CS(S)                                                    \
     if (momentum_only)                                                 \
-        k_collide_stream<S, true><<<grid, block, 0, st>>>(a);          \
+        k_collide_stream<S, true, false><<<grid, block, 0, st>>>(a);   \
+    else if (force)                                                    \
+        k_collide_stream<S, false, true><<<grid, block, 0, st>>>(a);   \
     else                                                               \
-        k_collide_stream<S, false><<<grid, block, 0, st>>>(a);
+        k_collide_stream<S, false, false><<<grid, block, 0, st>>>(a);
     switch (storage) {
     case LBM_F64: GBLBM_CS(LBM_F64); break;
     case LBM_F32: GBLBM_CS(LBM_F32); break;
