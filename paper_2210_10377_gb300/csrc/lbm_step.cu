@@ -142,13 +142,13 @@ template <> __device__ __forceinline__ float param<float>(double, float f) { ret
 // evaluated for opposite directions together: they share the even part
 // s = drho - 1.5 rho u^2 + 4.5 rho (c.u)^2 and differ in the sign of the odd
 // part 3 rho c.u.  ft = f + (feq - f)/tau, plus 3 w_i c_i.g with a body force.
-// ftr receives ft rounded to the storage type (the values that are stored).
+// out receives ft rounded to the storage type (the values that are stored).
 __device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double recip(double v) { return 1.0 / v; }
 
 template <int S, bool FORCE>
 __device__ __forceinline__ void collide_node(const StepArgs &a, const typename Traits<S>::comp_t (&g)[9],
-                                             typename Traits<S>::comp_t (&ftr)[9], bool &bad)
+                                             typename Traits<S>::store_t (&out)[9], bool &bad)
 {
     using ST = typename Traits<S>::store_t;
     using T = typename Traits<S>::comp_t;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void collide_node(const StepArgs &a, const typename T
         for (int i = 1; i < 9; ++i) v[i] += T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy);
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) ftr[i] = to_comp(to_store<ST>(v[i]));
+    for (int i = 0; i < 9; ++i) out[i] = to_store<ST>(v[i]);
 }
 
 // Control-volume contributions of one fluid node (x, y).
@@ -345,9 +345,13 @@ __device__ __forceinline__ void column_update(const StepArgs &a, int x, int y0,
                 ftr[i] = to_comp(sv);
             }
         } else if (!MOMENTUM_ONLY) {
-            collide_node<S, FORCE>(a, f[r], ftr, bad);
+            ST out[9];
+            collide_node<S, FORCE>(a, f[r], out, bad);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) dst[i * plane + idx] = to_store<ST>(ftr[i]);
+            for (int i = 0; i < 9; ++i) {
+                dst[i * plane + idx] = out[i];
+                ftr[i] = to_comp(out[i]);
+            }
         }
         if (cvtile) cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y, f[r], ftr, nb[r], acc);
     }
@@ -389,9 +393,13 @@ __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x,
                 ftr[i] = to_comp(sv);
             }
         } else if (!MOMENTUM_ONLY) {
-            collide_node<S, FORCE>(a, f[r], ftr, bad);
+            ST out[9];
+            collide_node<S, FORCE>(a, f[r], out, bad);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) o[r * pitch + i * plane] = to_store<ST>(ftr[i]);
+            for (int i = 0; i < 9; ++i) {
+                o[r * pitch + i * plane] = out[i];
+                if (cvtile) ftr[i] = to_comp(out[i]);
+            }
         }
         if (cvtile) cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r, f[r], ftr, 0, acc);
     }
@@ -566,7 +574,10 @@ __device__ __forceinline__ void tma_tile(const StepArgs &a, const typename Trait
                     f[i] = to_comp(sm[(i * C::BR + r + 1 - cy(i)) * C::SEG + (xs - x0) + C::PAD - cx(i)]);
                 }
             }
-            collide_node<S, FORCE>(a, f, ft[v], bad);
+            ST out[9];
+            collide_node<S, FORCE>(a, f, out, bad);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) ft[v][i] = to_comp(out[i]);
         }
         if (cvtile) cv_node<S, false, FORCE>(a, x, y, f, ft[v], nb, acc);
     }
