@@ -718,8 +718,8 @@ cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, i
         }
     }
     dim3 grid(tiles_x, tiles_y);
-    dim3 block(TILE_X, tile_rows(storage) / direct_rpt(storage));
     const bool force = a.gx != 0.0 || a.gy != 0.0;
+    dim3 block(TILE_X, tile_rows(storage) / direct_rpt(storage));
 #define GBLBM_CS(S)                                                    \
     if (momentum_only)                                                 \
         k_collide_stream<S, true, false><<<grid, block, 0, st>>>(a);   \
