@@ -37,6 +37,8 @@ def _stale(target, deps):
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    # GBLBM_NVCC_FLAGS: extra nvcc flags (tuning macros), e.g. "-DGBLBM_TMA_MINB=2"
+    extra_flags = list(extra_flags) + os.environ.get("GBLBM_NVCC_FLAGS", "").split()
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "gblbm.h"))
@@ -47,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     for s in srcs:
         o = os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
-        if force or _stale(o, [s] + headers):
+        if force or extra_flags or _stale(o, [s] + headers):
             jobs.append([cc, *ARCH, *FLAGS, *extra_flags, "-c", s, "-o", o])
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

@@ -405,8 +405,31 @@ __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x,
     }
 }
 
+// Minimum resident CTAs per SM asked of the compiler for the direct kernel
+// (0: no bound); tuning knobs.  FP16 storage is occupancy-bound: 8 CTAs of 128
+// threads (64 registers) run it faster than fewer CTAs without spills.
+#ifndef GBLBM_DIRECT_MINB_F16
+#define GBLBM_DIRECT_MINB_F16 8
+#endif
+#ifndef GBLBM_DIRECT_MINB_F32
+#define GBLBM_DIRECT_MINB_F32 0
+#endif
+template <int S> struct DirectMinBlocks {
+    static constexpr int value = 0;
+};
+template <> struct DirectMinBlocks<LBM_F32> {
+    static constexpr int value = GBLBM_DIRECT_MINB_F32;
+};
+template <> struct DirectMinBlocks<LBM_F32_DEV> {
+    static constexpr int value = GBLBM_DIRECT_MINB_F32;
+};
+template <> struct DirectMinBlocks<LBM_F16_DEV> {
+    static constexpr int value = GBLBM_DIRECT_MINB_F16;
+};
+
 template <int S, bool MOMENTUM_ONLY, bool FORCE>
-__global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S))) k_collide_stream(StepArgs a)
+__global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S)), DirectMinBlocks<S>::value)
+    k_collide_stream(StepArgs a)
 {
     constexpr int RPT = direct_rpt(S);
     using A = typename AccOf<S>::type;
@@ -506,6 +529,15 @@ __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, int x
 
 }  // namespace tma
 
+// Shared memory budget (KB) for the staged kernel's stages and the number of
+// its CTAs per SM; tuning knobs (two CTAs per SM hide each other's barriers).
+#ifndef GBLBM_TMA_SMEM_KB
+#define GBLBM_TMA_SMEM_KB 105
+#endif
+#ifndef GBLBM_TMA_MINB
+#define GBLBM_TMA_MINB 2
+#endif
+
 template <int S> struct TmaCfg {
     using ST = typename Traits<S>::store_t;
     static constexpr int TR = tile_rows(S);
@@ -517,7 +549,8 @@ template <int S> struct TmaCfg {
     static constexpr int THREADS = XT * TR;            // one tile row per thread
     static constexpr uint32_t BOX_BYTES = 9u * BR * SEG * (uint32_t)sizeof(ST);
     static constexpr uint32_t STAGE_BYTES = (BOX_BYTES + 127u) & ~127u;
-    static constexpr int NS = (200 * 1024) / STAGE_BYTES < 8 ? (200 * 1024) / STAGE_BYTES : 8;
+    static constexpr int NS_FIT = (GBLBM_TMA_SMEM_KB * 1024) / STAGE_BYTES;
+    static constexpr int NS = NS_FIT < 2 ? 2 : (NS_FIT > 8 ? 8 : NS_FIT);
     static constexpr size_t SMEM = (size_t)NS * STAGE_BYTES + 128 + 8 * NS;
     static_assert(NS >= 2, "at least two stages");
     static_assert(SEG * sizeof(ST) % 16 == 0, "box rows are whole 16-byte units");
@@ -602,7 +635,7 @@ __device__ __forceinline__ void tma_tile(const StepArgs &a, const typename Trait
 }
 
 template <int S, bool FORCE>
-__global__ void __launch_bounds__(TmaCfg<S>::THREADS, 1)
+__global__ void __launch_bounds__(TmaCfg<S>::THREADS, GBLBM_TMA_MINB)
     k_collide_stream_tma(const StepArgs a, int ntiles, const __grid_constant__ CUtensorMap map)
 {
     using C = TmaCfg<S>;
@@ -683,7 +716,7 @@ cudaError_t launch_tma_f(const StepArgs &a, int tiles, int sms, const void *map,
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    const int grid = tiles < sms ? tiles : sms;
+    const int grid = tiles < sms * GBLBM_TMA_MINB ? tiles : sms * GBLBM_TMA_MINB;
     k_collide_stream_tma<S, FORCE><<<grid, C::THREADS, C::SMEM, st>>>(a, tiles, *(const CUtensorMap *)map);
     return cudaGetLastError();
 }
