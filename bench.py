@@ -39,6 +39,8 @@ def args_():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--ref-seconds", type=float, default=None,
+                   help="time budget of the reference (oracle) arm; default from steps+warmup")
     p.add_argument("--profile", action="store_true",
                    help="only create the solver and run warm-up + K steps (for ncu captures)")
     p.add_argument("--workload", default=None, help="workload name (profile mode)")
@@ -53,6 +55,17 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduce_max(value, device=None):
+    """Max of a per-rank value over all ranks (the job's time is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -208,7 +221,7 @@ def run_reference(a):
         return 0
     from paper_2210_10377_gb300 import inputs
     w = inputs.LARGE_F32
-    budget = min(120.0, max(10.0, 0.5 * (a.steps + a.warmup)))
+    budget = a.ref_seconds if a.ref_seconds else min(120.0, max(10.0, 0.5 * (a.steps + a.warmup)))
     mlups, steps, el = oracle_sample(w, budget)
     line = {"metric": "MLUPS", "value": round(mlups, 3), "unit": "MLUPS", "impl": "reference",
             "n_gpus": a.gpus, "steps": steps, "warmup": 1, "ms_per_step": el / steps * 1e3,
@@ -255,9 +268,7 @@ def run_ours(a):
     launches = lat.launch_count - launches0
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = reduce_max(ms, device="cuda")
         torch.distributed.barrier()
     value = world * w.nodes * a.steps / (ms / 1e3) / 1e6
     rl = kernel_roofline(torch, lat, w, storage, min(a.steps, 2000), peak)
@@ -284,9 +295,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = reduce_max(e2e_s, device="cuda")
     e2e = {"value": round(world * w.nodes * a.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": round((w.nodes + 8) / a.steps, 3),
            "d2h_bytes_per_step": round((4 * 2 * 8 * a.steps + 9 * 8 * w.nodes) / a.steps, 3),
