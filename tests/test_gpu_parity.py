@@ -329,3 +329,41 @@ def test_staged_kernel_matches_direct_kernel(gb, storage):
         for s in ("DRTT", "DEFECT"):
             for k in (0, 1):
                 assert np.abs(a.force_series(s)[k] - b.force_series(s)[k]).max() <= 1e-12 * scale
+
+
+def test_allocation_failure_is_reported_and_cleaned_up(gb):
+    # fault injection on the host: an allocator hook that refuses the k-th request
+    import ctypes as C
+    import torch
+    L = gb.lib()
+    m = naca(inputs.SMALL_F64)
+    u = np.array([0.05])
+    for fail_at in (0, 1, 3, 8, 14):
+        live = {}
+        count = [0]
+
+        def alloc(nbytes, stream, user):
+            count[0] += 1
+            if count[0] > fail_at:
+                return None
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), 0, stream or 0)
+            live[p] = nbytes
+            return p
+
+        def free(ptr, user):
+            live.pop(ptr)
+            torch.cuda.caching_allocator_delete(ptr)
+
+        fa, ff = gb.ALLOC_FN(alloc), gb.FREE_FN(free)
+        bc = gb.lbm_bc()
+        L.lbm_bc_default(C.byref(bc))
+        bc.storage = gb.F32
+        bc.alloc, bc.free = fa, ff
+        h = C.c_void_p()
+        rc = L.lbm_create(m.ctypes.data_as(C.POINTER(C.c_uint8)), m.shape[1], m.shape[0], 0.6,
+                          gb._dp(u), 1, C.byref(bc), C.byref(h))
+        assert rc == 2 and not h.value, (fail_at, rc)
+        assert b"allocation" in L.lbm_last_error(None)
+        assert live == {}  # everything that was handed out was given back
+    lat = gb.Lattice(m, 0.6, 0.05, storage="f32")  # the device is still usable
+    lat.step(3)
