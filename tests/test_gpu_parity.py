@@ -367,3 +367,20 @@ def test_allocation_failure_is_reported_and_cleaned_up(gb):
         assert live == {}  # everything that was handed out was given back
     lat = gb.Lattice(m, 0.6, 0.05, storage="f32")  # the device is still usable
     lat.step(3)
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16dev", 1e-3)])
+def test_force_series_2000_steps_scaled_bench_geometry(gb, storage, tol):
+    # the bench geometry shrunk 8x (512 x 256, chord 32 at 4 deg, same tau): every
+    # scheme's per-step force over 2000 steps, against the FP64 oracle, on the
+    # scale of the largest drag or lift force of the window
+    w = inputs.scaled(inputs.LARGE_F32, 8, storage)
+    m = naca(w)
+    sim, lat = run_pair(gb, m, w.tau, w.u_in, 2000, storage=storage, chunks=[7, 1993])
+    scale = force_scale(sim)
+    for s in ("B", "DRTT", "A", "A_RTT"):
+        ox, oy = sim.force_series(ORACLE_SCHEME[s])
+        gx, gy = lat.force_series(s)
+        sc = max(scale, np.abs(ox).max()) if s in ("A", "A_RTT") else scale
+        assert np.abs(gx - ox).max() <= tol * sc, s
+        assert np.abs(gy - oy).max() <= tol * sc, s
