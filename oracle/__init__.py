@@ -55,6 +55,9 @@ def lib():
         L.oracle_force_series.restype = C.c_int
         L.oracle_drtt_parts.argtypes = [C.c_void_p, C.c_long, dp]
         L.oracle_drtt_parts.restype = C.c_int
+        L.oracle_adjoint.argtypes = [up, C.c_int, C.c_int, C.c_double, dp, dp, C.c_int, C.c_int,
+                                     C.c_double, C.c_double, dp, dp, dp, dp]
+        L.oracle_adjoint.restype = C.c_int
         _lib = L
     return _lib
 
@@ -195,3 +198,22 @@ class Sim:
         if lib().oracle_drtt_parts(self._h, int(t), _dp(out)) != 0:
             raise IndexError("step out of range")
         return out
+
+
+def adjoint(mask, tau, u_in, f0, steps, window, wx=1.0, wy=0.0):
+    """J = window-average of wx Fx + wy Fy (algorithm B) after `steps` steps from
+    f0, and dJ/dtau, dJ/du_in[ny], dJ/df0[9][ny][nx] (channel set-up)."""
+    mask = np.ascontiguousarray(mask, np.uint8)
+    ny, nx = mask.shape
+    u = np.ascontiguousarray(np.broadcast_to(np.asarray(u_in, np.float64), (ny,)))
+    f0 = np.ascontiguousarray(f0, np.float64).reshape(9, ny, nx)
+    J = np.zeros(1)
+    dtau = np.zeros(1)
+    du = np.zeros(ny)
+    df0 = np.zeros((9, ny, nx))
+    rc = lib().oracle_adjoint(_up(mask), nx, ny, float(tau), _dp(u), _dp(f0), int(steps),
+                              int(window), float(wx), float(wy), _dp(J), _dp(dtau), _dp(du),
+                              _dp(df0))
+    if rc != 0:
+        raise ValueError("oracle_adjoint rejected its arguments")
+    return float(J[0]), float(dtau[0]), du, df0

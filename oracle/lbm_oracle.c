@@ -517,3 +517,161 @@ int oracle_drtt_parts(const oracle_sim *s, long t, double *out6)
     memcpy(out6, s->jseries + t * 6, sizeof(double) * 6);
     return 0;
 }
+
+/* ------------------------------ discrete adjoint ------------------------------
+ * Gradient of the window-averaged force of algorithm B,
+ *   J = (1/M) sum_{t = T-M}^{T-1} (wx Fx(t) + wy Fy(t)),  F(t) = 2 sum_links c_i ft_i(x_f, t),
+ * with respect to the relaxation time tau, the inlet velocity of every row,
+ * and the initial pre-collision populations f(x, 0), for the channel set-up.
+ * The forward map of one step (collide, stream with halfway bounce-back, inlet,
+ * outlet) is differentiated exactly and transposed step by step, backwards in
+ * time; states are recomputed from sqrt(T)-spaced checkpoints.
+ *
+ * One step, with lt = dJ/d(ft(t)) and lam = dJ/d(f(t)):
+ *   lt_j(y) = lam'_j(y + c_j)        if y + c_j is a fluid node in the domain,
+ *           = lam'_opp(j)(y)         if y + c_j is solid (bounce-back),
+ *           + (2/M) (wx c_jx + wy c_jy) on links inside the window,
+ *   where lam' is lam(t+1) with the inlet column set to zero (overwritten by the
+ *   inlet), the outlet column set to zero and added to column nx-2 (the outlet
+ *   copies it);
+ *   lam_k(y) = sum_i lt_i(y) d ft_i / d f_k(y)   (collision Jacobian, entry by entry),
+ *   dJ/d omega += sum_i lt_i (feq_i - f_i),  omega = 1/tau,
+ *   inlet node: dJ/du_in(y) += sum_i lt_i d feq_i(rho0, (u_in(y), 0)) / du, lam = 0.
+ * ------------------------------------------------------------------------------ */
+
+/* d ft_i / d f_k of the BGK collision at one node, from feq_i = w_i rho
+ * (1 + 3 cu + 4.5 cu^2 - 1.5 u^2), u = j / rho:
+ *   d feq_i / d f_k = feq_i / rho + (d feq_i / d u) . (c_k - u) / rho. */
+static void collision_jacobian(const double *fi, double omega, double *Jm /* [9][9], Jm[i*9+k] */)
+{
+    double rho, jx, jy;
+    moments(fi, &rho, &jx, &jy);
+    double ux = jx / rho, uy = jy / rho;
+    double feq[9];
+    oracle_feq(rho, ux, uy, feq);
+    for (int i = 0; i < 9; ++i) {
+        double cu = OC_X[i] * ux + OC_Y[i] * uy;
+        double dux = O_W[i] * rho * (3.0 * OC_X[i] + 9.0 * cu * OC_X[i] - 3.0 * ux);
+        double duy = O_W[i] * rho * (3.0 * OC_Y[i] + 9.0 * cu * OC_Y[i] - 3.0 * uy);
+        for (int k = 0; k < 9; ++k) {
+            double dfeq = feq[i] / rho + (dux * (OC_X[k] - ux) + duy * (OC_Y[k] - uy)) / rho;
+            Jm[i * 9 + k] = (i == k ? 1.0 - omega : 0.0) + omega * dfeq;
+        }
+    }
+}
+
+/* mask, nx, ny, tau, u_in[ny], f0[9][ny][nx] (fluid nodes used): as oracle_create.
+ * Outputs: *J, *dJ_dtau, dJ_du[ny], dJ_df0[9][ny][nx] (NULL allowed).
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_adjoint(const unsigned char *mask, int nx, int ny, double tau, const double *u_in,
+                   const double *f0, int steps, int window, double wx, double wy, double *J,
+                   double *dJ_dtau, double *dJ_du, double *dJ_df0)
+{
+    if (steps < 1 || window < 1 || window > steps) return -1;
+    oracle_sim *s = oracle_create(mask, nx, ny, tau, u_in, ny, 0, 1.0, NULL, NULL);
+    if (!s) return -1;
+    const long N = s->N;
+    const size_t state = sizeof(double) * 9 * N;
+    int K = 1;
+    while ((long)K * K < steps) ++K;
+    int nck = (steps + K - 1) / K;
+    double *ck = (double *)malloc(state * (size_t)nck);      /* checkpoints f(kK) */
+    double *seg = (double *)malloc(state * (size_t)(K + 1)); /* f(t) of one segment */
+    double *lam = (double *)calloc(9 * N, sizeof(double));
+    double *lamp = (double *)calloc(9 * N, sizeof(double));
+    double *lt = (double *)calloc(9 * N, sizeof(double));
+    if (!ck || !seg || !lam || !lamp || !lt || grow_series(s, steps)) {
+        free(ck); free(seg); free(lam); free(lamp); free(lt);
+        oracle_destroy(s);
+        return -1;
+    }
+    oracle_set_populations(s, f0);
+    /* forward: checkpoints and the force series */
+    for (int t = 0; t < steps; ++t) {
+        if (t % K == 0) memcpy(ck + (size_t)(t / K) * 9 * N, s->f, state);
+        step_once(s);
+    }
+    double Jv = 0.0;
+    for (int t = steps - window; t < steps; ++t)
+        Jv += wx * s->series[t * NSCHEME * 2 + SCHEME_B * 2 + 0] +
+              wy * s->series[t * NSCHEME * 2 + SCHEME_B * 2 + 1];
+    Jv /= window;
+
+    double domega = 0.0;
+    double *du = (double *)calloc(ny, sizeof(double));
+    const double obj = 2.0 / window;
+    /* lam holds dJ/df(t+1); zero at t+1 = T */
+    for (int k = nck - 1; k >= 0; --k) {
+        int t0 = k * K, t1 = (k + 1) * K < steps ? (k + 1) * K : steps;
+        /* recompute f(t0 .. t1-1) (rewriting the same series entries) */
+        memcpy(s->f, ck + (size_t)k * 9 * N, state);
+        s->t = t0;
+        for (int t = t0; t < t1; ++t) {
+            memcpy(seg + (size_t)(t - t0) * 9 * N, s->f, state);
+            if (t + 1 < t1) step_once(s);
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const double *f = seg + (size_t)(t - t0) * 9 * N;
+            /* lam' = lam(t+1) with the inlet and outlet columns folded */
+            memcpy(lamp, lam, sizeof(double) * 9 * N);
+            for (int y = 0; y < ny; ++y) {
+                long n0 = (long)y * nx, n1 = n0 + nx - 1, n2 = n1 - 1;
+                for (int i = 0; i < 9; ++i) {
+                    lamp[i * N + n2] += lamp[i * N + n1];
+                    lamp[i * N + n1] = 0.0;
+                    lamp[i * N + n0] = 0.0;
+                }
+            }
+            int in_window = t >= steps - window;
+            for (long n = 0; n < N; ++n) {
+                if (mask[n]) continue;
+                int x = (int)(n % nx), y = (int)(n / nx);
+                for (int j = 0; j < 9; ++j) {
+                    long m = j == 0 ? n : neighbour(nx, ny, 0, x, y, j);
+                    double v = 0.0;
+                    if (m >= 0) {
+                        if (mask[m]) {
+                            v = lamp[O_OPP[j] * N + n];
+                            if (in_window) v += obj * (wx * OC_X[j] + wy * OC_Y[j]);
+                        } else {
+                            v = lamp[j * N + m];
+                        }
+                    }
+                    lt[j * N + n] = v;
+                }
+            }
+            for (long n = 0; n < N; ++n) {
+                for (int i = 0; i < 9; ++i) lam[i * N + n] = 0.0;
+                if (mask[n]) continue;
+                int x = (int)(n % nx), y = (int)(n / nx);
+                if (x == 0) {
+                    double u = s->u_in[y];
+                    for (int i = 0; i < 9; ++i)
+                        du[y] += lt[i * N + n] * O_W[i] * 1.0 *
+                                 (3.0 * OC_X[i] + 9.0 * OC_X[i] * OC_X[i] * u - 3.0 * u);
+                    continue;
+                }
+                double fi[9], Jm[81], rho, jx, jy, feq[9];
+                for (int i = 0; i < 9; ++i) fi[i] = f[i * N + n];
+                collision_jacobian(fi, s->omega, Jm);
+                moments(fi, &rho, &jx, &jy);
+                oracle_feq(rho, jx / rho, jy / rho, feq);
+                for (int k2 = 0; k2 < 9; ++k2) {
+                    double acc = 0.0;
+                    for (int i = 0; i < 9; ++i) acc += lt[i * N + n] * Jm[i * 9 + k2];
+                    lam[k2 * N + n] = acc;
+                }
+                for (int i = 0; i < 9; ++i) domega += lt[i * N + n] * (feq[i] - fi[i]);
+            }
+        }
+    }
+    if (J) *J = Jv;
+    if (dJ_dtau) *dJ_dtau = -domega / (tau * tau);
+    if (dJ_du) memcpy(dJ_du, du, sizeof(double) * ny);
+    if (dJ_df0)
+        for (int i = 0; i < 9; ++i)
+            for (long n = 0; n < N; ++n) dJ_df0[i * N + n] = mask[n] ? 0.0 : lam[i * N + n];
+    free(du); free(ck); free(seg); free(lam); free(lamp); free(lt);
+    oracle_destroy(s);
+    return 0;
+}
