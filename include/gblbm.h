@@ -183,6 +183,24 @@ lbm_status lbm_control_volume(lbm_ctx *h, int *cv);
 lbm_status lbm_naca_mask(int nx, int ny, double chord, double thickness, double alpha_deg,
                          double xc, double yc, int closed_te, uint8_t *out);
 
+/* Discrete adjoint (channel set-up, no body force, record_series = 1).
+ * From the current state (step T0) run `steps` steps as lbm_step would (the
+ * handle ends at T0 + steps with its force series), and return the objective
+ *   J = (1/window) sum_{t = T0+steps-window}^{T0+steps-1} (wx Fx(t) + wy Fy(t)),
+ * F the algorithm-B force (Eq. rtt5 with bounce-back), with its gradients:
+ *   dJ_dtau     dJ/dtau;
+ *   dJ_du[ny]   dJ/du_in(y) through the equilibrium inlet of every row;
+ *   dJ_df0      [9][ny][nx] dJ/df(x, T0), pre-collision state at T0 (0 on solid
+ *               nodes and in the inlet column, which do not enter J).
+ * Every step of the forward map (BGK collision, pull streaming with halfway
+ * bounce-back, inlet, outlet) is differentiated exactly and transposed, in the
+ * storage's compute precision; states are recomputed from checkpoints every
+ * checkpoint_every steps (<= 0: ceil(sqrt(steps))).  Any output may be NULL.
+ * EINVAL for a periodic domain, a body force, record_series = 0, or
+ * window outside [1, steps]. */
+lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, int checkpoint_every,
+                       double *J, double *dJ_dtau, double *dJ_du, double *dJ_df0);
+
 /* Number of completed steps T. */
 long lbm_steps_done(const lbm_ctx *h);
 

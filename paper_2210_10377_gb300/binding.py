@@ -66,6 +66,7 @@ def lib():
     L.lbm_control_volume.argtypes = [vp, ip]
     L.lbm_naca_mask.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                 C.c_double, C.c_double, C.c_int, C.POINTER(C.c_uint8)]
+    L.lbm_adjoint.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
     L.lbm_steps_done.argtypes = [vp]
     L.lbm_steps_done.restype = C.c_long
     L.lbm_num_links.argtypes = [vp]
@@ -80,7 +81,7 @@ def lib():
     L.lbm_destroy.restype = None
     for name in ("lbm_create", "lbm_step", "lbm_force", "lbm_force_series", "lbm_populations",
                  "lbm_set_populations", "lbm_links", "lbm_control_volume", "lbm_naca_mask",
-                 "lbm_set_kernel_timing", "lbm_kernel_times"):
+                 "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_adjoint"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -233,6 +234,17 @@ class Lattice:
         cv = (C.c_int * 4)()
         _check(lib().lbm_control_volume(self._h, cv), self._h)
         return list(cv)
+
+    def adjoint(self, steps, window, wx=1.0, wy=0.0, checkpoint_every=0, want_df0=True):
+        """Run `steps` steps and return (J, dJ/dtau, dJ/du_in[ny], dJ/df0[9][ny][nx] or
+        None) for J = the window-averaged wx Fx + wy Fy of algorithm B."""
+        J, dtau = C.c_double(), C.c_double()
+        du = np.zeros(self.ny)
+        df0 = np.zeros((9, self.ny, self.nx)) if want_df0 else None
+        _check(lib().lbm_adjoint(self._h, int(steps), int(window), float(wx), float(wy),
+                                 int(checkpoint_every), C.byref(J), C.byref(dtau), _dp(du),
+                                 _dp(df0) if df0 is not None else None), self._h)
+        return J.value, dtau.value, du, df0
 
     @property
     def steps_done(self):

@@ -962,6 +962,167 @@ lbm_status lbm_naca_mask(int nx, int ny, double chord, double thickness, double 
     return LBM_OK;
 }
 
+lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, int checkpoint_every,
+                       double *J, double *dJ_dtau, double *dJ_du, double *dJ_df0)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (steps < 1 || window < 1 || window > steps)
+        return set_err(h, LBM_EINVAL, "need 1 <= window <= steps (got %d, %d)", window, steps);
+    if (h->periodic) return set_err(h, LBM_EINVAL, "the adjoint covers the channel set-up only");
+    if (h->g[0] != 0.0 || h->g[1] != 0.0)
+        return set_err(h, LBM_EINVAL, "the adjoint does not cover a body force");
+    if (!h->record_series) return set_err(h, LBM_EINVAL, "the adjoint needs record_series = 1");
+    if (!std::isfinite(wx) || !std::isfinite(wy)) return set_err(h, LBM_EINVAL, "weights not finite");
+    int K = checkpoint_every;
+    if (K <= 0) {
+        K = 1;
+        while ((long long)K * K < steps) ++K;
+    }
+    if (K > steps) K = steps;
+    const int nck = (steps + K - 1) / K;
+    const size_t buf_bytes = 9 * (size_t)h->plane * h->elem;
+    const size_t comp = h->storage == LBM_F64 ? 8 : 4;
+    const size_t comp_bytes = 9 * (size_t)h->plane * comp;
+    const int nblk = adjoint_blocks(h->nx, h->ny);
+    cudaStream_t st = h->stream;
+
+    std::vector<void *> owned;
+    auto grab = [&](size_t bytes) {
+        void *p = dev_alloc(h, bytes);
+        if (p) owned.push_back(p);
+        return p;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (void *p : owned) dev_free(h, p);
+        owned.clear();
+    };
+    char *ck = (char *)grab(buf_bytes * nck);
+    char *seg = (char *)grab(comp_bytes * K);
+    char *lam_a = (char *)grab(comp_bytes), *lam_b = (char *)grab(comp_bytes);
+    const size_t guard_front = 256, guard_back = 2048;
+    char *sbase0 = (char *)grab(guard_front + buf_bytes + guard_back);
+    char *sbase1 = (char *)grab(guard_front + buf_bytes + guard_back);
+    double *part = (double *)grab(sizeof(double) * CV_PARTIAL * h->n_cv_tiles);
+    double *du_acc = (double *)grab(sizeof(double) * h->ny);
+    double *dw_acc = (double *)grab(sizeof(double) * nblk);
+    double *dw_out = (double *)grab(sizeof(double));
+    if (!ck || !seg || !lam_a || !lam_b || !sbase0 || !sbase1 || !part || !du_acc || !dw_acc || !dw_out) {
+        release();
+        return set_err(h, LBM_ENOMEM, "adjoint: allocation of checkpoints / work arrays failed");
+    }
+    std::vector<int> ckpre(nck);
+    const long long T0 = h->t;
+    lbm_status rs = LBM_OK;
+    // forward: checkpoint, then K steps
+    for (int k = 0; k < nck; ++k) {
+        cudaError_t e = cudaMemcpyAsync(ck + buf_bytes * k, h->pop[h->cur], buf_bytes,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            release();
+            return cuda_err(h, e, "adjoint: checkpoint copy");
+        }
+        ckpre[k] = h->precollision;
+        const int n = (k + 1) * K <= steps ? K : steps - k * K;
+        rs = lbm_step(h, n);
+        if (rs != LBM_OK) {
+            release();
+            return rs;
+        }
+    }
+    // J from the algorithm-B series of the window
+    {
+        std::vector<double> fx(window), fy(window);
+        rs = lbm_force_series(h, LBM_FORCE_MEA_B, (long)(T0 + steps - window), window, fx.data(),
+                              fy.data());
+        if (rs != LBM_OK) {
+            release();
+            return rs;
+        }
+        double s = 0.0;
+        for (int k = 0; k < window; ++k) s += wx * fx[k] + wy * fy[k];
+        if (J) *J = s / window;
+    }
+    // backward over the segments, each recomputed from its checkpoint
+    cudaError_t e = cudaMemsetAsync(lam_b, 0, comp_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lam_a, 0, comp_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(du_acc, 0, sizeof(double) * h->ny, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dw_acc, 0, sizeof(double) * nblk, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sbase0, 0, guard_front + buf_bytes + guard_back, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sbase1, 0, guard_front + buf_bytes + guard_back, st);
+    char *lam_next = lam_b, *lam_cur = lam_a;  // lam(T) = 0
+    const double obj_x = 2.0 * wx / window, obj_y = 2.0 * wy / window;
+    for (int k = nck - 1; k >= 0 && e == cudaSuccess; --k) {
+        const int t0 = k * K;
+        const int n = (k + 1) * K <= steps ? K : steps - t0;
+        char *s_cur = sbase0 + guard_front, *s_nxt = sbase1 + guard_front;
+        e = cudaMemcpyAsync(s_cur, ck + buf_bytes * k, buf_bytes, cudaMemcpyDeviceToDevice, st);
+        int pre = ckpre[k];
+        for (int s = 0; s < n && e == cudaSuccess; ++s) {
+            e = launch_precollision(h->storage, s_cur, h->nbits, h->plane, h->nx, h->ny, h->pitch, pre,
+                                    seg + comp_bytes * s, st);
+            if (e == cudaSuccess && s + 1 < n) {
+                StepArgs sa = step_args(h, h->cur, next_buf(h->cur), pre);
+                sa.src = s_cur;
+                sa.dst = s_nxt;
+                sa.partials = part;
+                sa.use_bulk = 0;
+                e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false, nullptr, st);
+                char *tmp = s_cur;
+                s_cur = s_nxt;
+                s_nxt = tmp;
+                pre = 0;
+                h->launches += 1;
+            }
+            h->launches += 1;
+        }
+        for (int s = n - 1; s >= 0 && e == cudaSuccess; --s) {
+            const int t = t0 + s;
+            e = launch_adjoint_step(h->storage, seg + comp_bytes * s, lam_next, lam_cur, h->nbits, h->u_row,
+                                    du_acc, dw_acc, h->plane, h->nx, h->ny, h->pitch,
+                                    t >= steps - window, h->omega, h->rho0, obj_x, obj_y, st);
+            char *tmp = lam_next;
+            lam_next = lam_cur;
+            lam_cur = tmp;
+            h->launches += 1;
+        }
+    }
+    if (e == cudaSuccess) e = launch_sum_serial(dw_acc, nblk, dw_out, st);
+    double dw = 0.0;
+    std::vector<double> du(h->ny);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&dw, dw_out, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(du.data(), du_acc, sizeof(double) * h->ny, cudaMemcpyDeviceToHost, st);
+    std::vector<char> lam_host;
+    if (e == cudaSuccess && dJ_df0) {
+        lam_host.resize(comp_bytes);
+        e = cudaMemcpyAsync(lam_host.data(), lam_next, comp_bytes, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_err(h, e, "adjoint");
+    if (dJ_dtau) *dJ_dtau = -dw / (h->tau * h->tau);
+    if (dJ_du)
+        for (int y = 0; y < h->ny; ++y) dJ_du[y] = du[y];
+    if (dJ_df0) {
+        // lam(T0) = dJ/df(T0) on fluid nodes; the inlet column and solid nodes do not enter J
+        const size_t N = (size_t)h->nx * h->ny;
+        std::vector<uint8_t> mask(N);
+        cudaError_t me = cudaMemcpy(mask.data(), h->mask_d, N, cudaMemcpyDeviceToHost);
+        if (me != cudaSuccess) return cuda_err(h, me, "adjoint: mask read-back");
+        for (int i = 0; i < 9; ++i)
+            for (int y = 0; y < h->ny; ++y)
+                for (int x = 0; x < h->nx; ++x) {
+                    const size_t src = (size_t)i * h->plane + (size_t)y * h->pitch + x;
+                    double v = comp == 8 ? ((const double *)lam_host.data())[src]
+                                         : (double)((const float *)lam_host.data())[src];
+                    if (mask[(size_t)y * h->nx + x] || x == 0) v = 0.0;
+                    dJ_df0[(size_t)i * N + (size_t)y * h->nx + x] = v;
+                }
+    }
+    return LBM_OK;
+}
+
 long lbm_steps_done(const lbm_ctx *h) { return h ? (long)h->t : -1; }
 
 long lbm_num_links(const lbm_ctx *h) { return h ? (long)h->nlinks : -1; }

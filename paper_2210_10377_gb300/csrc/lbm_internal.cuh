@@ -179,4 +179,16 @@ cudaError_t launch_scatter_pop(int storage, void *pop, const uint16_t *nbits, lo
                                int nx, int ny, int pitch, double rho0, int plane_i,
                                const double *in, cudaStream_t st);
 
+// discrete adjoint (lbm_adjoint.cu)
+cudaError_t launch_precollision(int storage, const void *src, const uint16_t *nbits, long long plane,
+                                int nx, int ny, int pitch, int precollision, void *out,
+                                cudaStream_t st);
+int adjoint_blocks(int nx, int ny);
+cudaError_t launch_adjoint_step(int storage, const void *fpre, const void *lam_next, void *lam,
+                                const uint16_t *nbits, const double *u_row, double *du_acc,
+                                double *dw_acc, long long plane, int nx, int ny, int pitch,
+                                int in_window, double omega, double rho0, double obj_x,
+                                double obj_y, cudaStream_t st);
+cudaError_t launch_sum_serial(const double *v, long long n, double *out, cudaStream_t st);
+
 }  // namespace gblbm

@@ -1,0 +1,114 @@
+"""The discrete adjoint on the GPU (lbm_adjoint, through the C ABI) against the
+FP64 CPU oracle's adjoint and against central finite differences of the GPU's
+own FP64 forward; at the differentiation workload (512 x 256, chord 64 at
+2 deg, Re 200, 4000 steps, drag averaged over the last 1000) the FP32 adjoint's
+gradients must lie within 1e-3 relative of central differences."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_10377_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_10377_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def small_case(seed=5):
+    ny, nx = 24, 48
+    m = np.zeros((ny, nx), np.uint8)
+    m[8:16, 16:26] = inputs.random_blobs_mask(10, 8, 3, seed=seed, max_radius=2.5, margin_x=0)
+    m[11, 20] = 1
+    u = inputs.random_inlet(ny, seed=seed + 1)
+    f0 = oracle.Sim(m, 0.7, u).populations() * inputs.perturbation(nx, ny, seed=seed + 2)
+    return m, u, f0
+
+
+def gpu_adjoint(gb, m, tau, u, f0, steps, window, wx, wy, storage, K=0):
+    lat = gb.Lattice(m, tau, u, storage=storage)
+    lat.set_populations(f0)
+    out = lat.adjoint(steps, window, wx, wy, checkpoint_every=K)
+    lat.close()
+    return out
+
+
+@pytest.mark.parametrize("K", [0, 7, 1, 200])
+def test_f64_adjoint_matches_oracle_adjoint(gb, K):
+    m, u, f0 = small_case()
+    steps, window, tau = 90, 40, 0.7
+    Jo, dto, duo, dfo = oracle.adjoint(m, tau, u, f0, steps, window, 0.8, 0.6)
+    Jg, dtg, dug, dfg = gpu_adjoint(gb, m, tau, u, f0, steps, window, 0.8, 0.6, "f64", K)
+    assert Jg == pytest.approx(Jo, rel=1e-12, abs=1e-15)
+    assert dtg == pytest.approx(dto, rel=1e-9)
+    assert np.abs(dug - duo).max() <= 1e-9 * np.abs(duo).max()
+    assert np.abs(dfg - dfo).max() <= 1e-9 * np.abs(dfo).max()
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-3), ("f32dev", 1e-3)])
+def test_reduced_precision_adjoint_matches_oracle(gb, storage, tol):
+    w = inputs.scaled(inputs.DIFF, 4)  # 128 x 64, chord 16 at 2 deg, same tau
+    m = oracle.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
+    u = np.full(w.ny, w.u_in)
+    f0 = oracle.Sim(m, w.tau, u).populations() * inputs.perturbation(w.nx, w.ny, seed=2210)
+    steps, window = 800, 200
+    Jo, dto, duo, dfo = oracle.adjoint(m, w.tau, u, f0, steps, window, 1.0, 0.0)
+    Jg, dtg, dug, dfg = gpu_adjoint(gb, m, w.tau, u, f0, steps, window, 1.0, 0.0, storage)
+    assert abs(Jg - Jo) <= tol * abs(Jo)
+    assert abs(dtg - dto) <= tol * abs(dto)
+    assert np.abs(dug - duo).max() <= tol * np.abs(duo).max()
+    assert np.abs(dfg - dfo).max() <= tol * np.abs(dfo).max()
+
+
+def test_differentiation_workload_against_central_differences(gb):
+    w = inputs.DIFF
+    m = gb.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
+    u = np.full(w.ny, w.u_in)
+    base = gb.Lattice(m, w.tau, u, storage="f64")
+    f0 = base.populations() * inputs.perturbation(w.nx, w.ny, seed=2210)
+    base.close()
+    steps, window = w.steps, 1000
+
+    def J64(tau=w.tau, uu=u):
+        lat = gb.Lattice(m, tau, uu, storage="f64")
+        lat.set_populations(f0)
+        lat.step(steps)
+        fx, _ = lat.force_series("B", steps - window, window)
+        lat.close()
+        return fx.mean()
+
+    J, dtau, du, df0 = gpu_adjoint(gb, m, w.tau, u, f0, steps, window, 1.0, 0.0, "f32")
+    assert np.isfinite(dtau) and np.all(np.isfinite(du)) and np.all(np.isfinite(df0))
+    h = 1e-5
+    fd = (J64(tau=w.tau + h) - J64(tau=w.tau - h)) / (2 * h)
+    assert abs(dtau - fd) <= 1e-3 * abs(fd)
+    for r in (w.ny // 2, w.ny // 4, 3):
+        up, um = u.copy(), u.copy()
+        up[r] += h
+        um[r] -= h
+        fdu = (J64(uu=up) - J64(uu=um)) / (2 * h)
+        assert abs(du[r] - fdu) <= 1e-3 * np.abs(du).max(), r
+    assert abs(J - J64()) <= 1e-4 * abs(J)
+
+
+def test_autograd_function(gb):
+    import torch
+    from paper_2210_10377_gb300.autograd import force_objective
+    m, u, f0 = small_case(9)
+    f = torch.tensor(f0, dtype=torch.float64, requires_grad=True)
+    tau = torch.tensor(0.7, dtype=torch.float64, requires_grad=True)
+    uu = torch.tensor(u, dtype=torch.float64, requires_grad=True)
+    J = force_objective(f, tau, uu, m, 60, 30, 1.0, 0.0, "f64")
+    (3.0 * J).backward()
+    Jo, dto, duo, dfo = oracle.adjoint(m, 0.7, u, f0, 60, 30, 1.0, 0.0)
+    assert float(J) == pytest.approx(Jo, rel=1e-12)
+    assert float(tau.grad) == pytest.approx(3 * dto, rel=1e-9)
+    assert np.abs(uu.grad.numpy() - 3 * duo).max() <= 1e-9 * np.abs(duo).max()
+    assert np.abs(f.grad.numpy() - 3 * dfo).max() <= 1e-9 * np.abs(dfo).max()
