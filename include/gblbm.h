@@ -139,8 +139,12 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
  * pull-stream + bounce-back + inlet/outlet + BGK collision kernel (which also
  * accumulates J(t) and the control-volume fluxes), then the link kernel (MEA
  * A, A', B of step t and DRTT of step t-1).  Blocks until the work is done.
+ * The call may be split into any sequence of calls with the same total: the
+ * state and the force series do not depend on the split.
  * EUNSTABLE if any step produced rho <= 0 or NaN (the state then holds the
- * result after all n steps). */
+ * result after all n steps); ETIMEOUT if a bounded wait of the staged kernel
+ * expired; ESTATE if a series row would have fallen outside the series buffer
+ * (an internal invariant; the row is dropped rather than written). */
 lbm_status lbm_step(lbm_ctx *h, int n);
 
 /* Force on the body (+x downstream) of the last completed step t = T-1

@@ -335,6 +335,8 @@ LinkArgs link_args(lbm_ctx *h, int src, int dst, int precollision, int drtt_only
     a.ticket = h->ticket;
     a.n_ctas = h->link_ctas;
     a.series = h->series;
+    a.series_rows = h->series_cap;
+    a.status = h->status;
     a.carry = h->carry;
     a.step_ctr = h->step_ctr;
     a.plane = h->plane;
@@ -394,7 +396,7 @@ cudaError_t join_side(lbm_ctx *h)
 
 void drop_graphs(lbm_ctx *h)
 {
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < NBUF; ++p)
         for (int k = 0; k < 2; ++k)
             if (h->graph[p][k]) {
                 cudaGraphExecDestroy(h->graph[p][k]);
@@ -814,6 +816,8 @@ lbm_status lbm_step(lbm_ctx *h, int n)
        "D2H status");
     CK(h, cudaStreamSynchronize(h->stream), "step sync");
     if (h->t - 1 > h->carry_from) h->drtt_ready = h->t - 1 > h->drtt_ready ? h->t - 1 : h->drtt_ready;
+    if (status[0] & 4)
+        return set_err(h, LBM_ESTATE, "a force-series row lay beyond the series buffer");
     if (status[0] & 2)
         return set_err(h, LBM_ETIMEOUT, "a bounded wait for staged copies expired");
     if (status[0]) return set_err(h, LBM_EUNSTABLE, "rho <= 0 or NaN first seen at step %d", status[1]);

@@ -132,6 +132,8 @@ struct LinkArgs {
     unsigned int *ticket;
     int n_ctas;
     double *series;
+    long long series_rows;   // rows the series holds; a row beyond sets status bit 4
+    int *status;             // [0]: error bits, as in StepArgs
     double *carry;           // J_post(t-1)[2], GL(t-1)[2], have_prev
     long long *step_ctr;
     long long plane;

@@ -892,26 +892,42 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
 #pragma unroll
         for (int k = 0; k < LINK_PARTIAL; ++k) d[k] = acc_double(w[k]);
         const long long t = *a.step_ctr;
-        auto row = [&](long long s) {
-            return a.series + SERIES_ROW * (a.record_series ? s : (s & 1));
-        };
+        // Series slot of a step: the step itself, or its parity when only the
+        // last two rows are kept.  A slot beyond the buffer (an internal
+        // invariant: the host grows the series before every launch) is not
+        // written and raises status bit 4.  The guard is a plain branch around
+        // the global stores; the stores never go through a pointer that could
+        // also refer to a thread-local array, nor is the address of the kernel
+        // parameter taken (that form lost stores in testing).
+        const bool keep_all = a.record_series != 0;
+        const long long rows = a.series_rows;
         // DRTT(t-1) = J(t-1) - J(t) + (gained - lost)(t-1), Eq. rtt7, with
         // J(t-1) on the post-collision state and J(t) on the pre-collision one
         if (a.carry[4] != 0.0 && t >= 1) {
-            double *q = row(t - 1);
-            q[4] = (a.carry[0] - d[6]) + a.carry[2];
-            q[5] = (a.carry[1] - d[7]) + a.carry[3];
+            const long long k = keep_all ? t - 1 : ((t - 1) & 1);
+            if (k < rows) {
+                double *q = a.series + SERIES_ROW * k;
+                q[4] = (a.carry[0] - d[6]) + a.carry[2];
+                q[5] = (a.carry[1] - d[7]) + a.carry[3];
+            } else {
+                atomicOr(a.status, 4);
+            }
         }
         if (!a.drtt_only) {
-            double *r = row(t);
-            r[0] = d[0] + a.link_base[0];
-            r[1] = d[1] + a.link_base[1];
-            r[2] = d[2] + a.link_base[0];
-            r[3] = d[3] + a.link_base[1];
-            r[6] = d[4] + a.link_base[0];
-            r[7] = d[5] + a.link_base[1];
-            r[8] = d[6] - d[8];
-            r[9] = d[7] - d[9];
+            const long long k = keep_all ? t : (t & 1);
+            if (k < rows) {
+                double *r = a.series + SERIES_ROW * k;
+                r[0] = d[0] + a.link_base[0];
+                r[1] = d[1] + a.link_base[1];
+                r[2] = d[2] + a.link_base[0];
+                r[3] = d[3] + a.link_base[1];
+                r[6] = d[4] + a.link_base[0];
+                r[7] = d[5] + a.link_base[1];
+                r[8] = d[6] - d[8];
+                r[9] = d[7] - d[9];
+            } else {
+                atomicOr(a.status, 4);
+            }
             a.carry[0] = d[8];
             a.carry[1] = d[9];
             a.carry[2] = d[10] + a.flux_base[0];

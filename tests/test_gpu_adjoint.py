@@ -76,8 +76,8 @@ def test_differentiation_workload_against_central_differences(gb):
     base.close()
     steps, window = w.steps, 1000
 
-    def J64(tau=w.tau, uu=u):
-        lat = gb.Lattice(m, tau, uu, storage="f64")
+    def J64(tau=w.tau, uu=u, storage="f64"):
+        lat = gb.Lattice(m, tau, uu, storage=storage)
         lat.set_populations(f0)
         lat.step(steps)
         fx, _ = lat.force_series("B", steps - window, window)
@@ -95,7 +95,11 @@ def test_differentiation_workload_against_central_differences(gb):
         um[r] -= h
         fdu = (J64(uu=up) - J64(uu=um)) / (2 * h)
         assert abs(du[r] - fdu) <= 1e-3 * np.abs(du).max(), r
-    assert abs(J - J64()) <= 1e-4 * abs(J)
+    # the adjoint's forward (checkpointed, stepped in segments) is the FP32
+    # forward of one lbm_step call; FP32 storage itself departs from FP64 by a
+    # few 1e-4 of the mean drag over 4000 steps, inside the 1e-3 gradient bar
+    assert abs(J - J64(storage="f32")) <= 1e-12 * abs(J)
+    assert abs(J - J64()) <= 1e-3 * abs(J)
 
 
 def test_autograd_function(gb):
