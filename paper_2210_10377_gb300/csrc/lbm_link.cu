@@ -1,0 +1,309 @@
+// lbm_link.cu -- the per-step force kernel and the population read-back.
+//
+// k_link_force: CTAs share the fluid-solid link list and reduce the momentum
+//   exchange of step t for algorithms A, A' and B (Eqs. MEA, rtt4, rtt5), fold
+//   the control-volume partials into J(t), and the last CTA to finish completes
+//   DRTT(t-1) = J(t-1) - J(t) + GL(t-1) (Eq. rtt7).
+// k_gather / k_scatter: one population plane between the device storage and
+//   an FP64 [ny][nx] array (pre-collision f(x, T) reconstructed by a pull).
+//
+// Reductions are deterministic (fixed trees, no floating-point atomics).
+#include "lbm_device.cuh"
+
+namespace gblbm {
+
+// ---------------------------------------------------------------------------
+// Link force + finalisation.  n_ctas CTAs of LINK_THREADS threads share the
+// links (contiguous chunks) and the control-volume partials; each writes one
+// partial row.  The last CTA to finish (atomic ticket) sums the rows in slot
+// order, so the result does not depend on which CTA finishes last, and
+// completes the step's series row and the DRTT of the previous step.
+// Series row t: A(2) B(2) DRTT(2) A'(2) defect(2), where defect is the
+// collision's momentum defect inside the box, J_pre(t) - J_post(t).
+// For deviation storage the momentum of the base w_i rho0 over the links and
+// over the box-surface crossings is a fixed geometric sum (link_base,
+// flux_base, from the host) added at the end.
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
+{
+    using ST = typename Traits<S>::store_t;
+    using T = typename Traits<S>::comp_t;
+    using A = typename AccOf<S>::type;
+    const ST *__restrict__ src = (const ST *)a.src;
+    const ST *__restrict__ dst = (const ST *)a.dst;
+    const long long plane = a.plane;
+    // v: A(2), B(2), A'(2), J_pre(2), J_post(2), GL(2)
+    A v[LINK_PARTIAL];
+#pragma unroll
+    for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(v[k]);
+    const long long per = (a.nlinks + gridDim.x - 1) / gridDim.x;
+    const long long k0 = per * blockIdx.x;
+    const long long k1 = k0 + per < a.nlinks ? k0 + per : a.nlinks;
+    if (!a.drtt_only) {
+        for (long long k = k0 + threadIdx.x; k < k1; k += LINK_THREADS) {
+            const int l = a.links[k];
+            const int n = l >> 3;
+            const int i = (l & 7) + 1;
+            const int o = opp(i);
+            const int x = n % a.nx, y = n / a.nx;
+            const long long idx = (long long)y * a.pitch + x;
+            T fi, fo;
+            if (a.precollision) {
+                fi = to_comp(src[i * plane + idx]);
+                fo = to_comp(src[o * plane + idx]);
+            } else {
+                // f_i(x_f, t): pulled from x_f - c_i, or bounced when that node is solid
+                if (a.nbits[idx] & (1u << o)) {
+                    fi = to_comp(src[o * plane + idx]);
+                } else {
+                    int sx = x - cx(i), sy = y - cy(i);
+                    if (a.periodic) sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+                    sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+                    fi = to_comp(src[i * plane + (long long)sy * a.pitch + sx]);
+                }
+                // f_opp(i)(x_f, t): x_f + c_i is solid, so it is the bounced ft_i(x_f, t-1)
+                fo = to_comp(src[i * plane + idx]);
+            }
+            const T ft = to_comp(dst[i * plane + idx]);
+            A sa, sb, sp;
+            if constexpr (S == LBM_F64) {
+                sa = fi + fo;
+                sb = 2.0 * ft;
+                sp = fi + ft;
+            } else {
+                sa = ff_two_sum(fi, fo);
+                sb = {2.0f * ft, 0.0f};
+                sp = ff_two_sum(fi, ft);
+            }
+            const int ex = cx(i), ey = cy(i);
+            if (ex != 0) {
+                acc_add(v[0], ex > 0 ? sa : -sa);
+                acc_add(v[2], ex > 0 ? sb : -sb);
+                acc_add(v[4], ex > 0 ? sp : -sp);
+            }
+            if (ey != 0) {
+                acc_add(v[1], ey > 0 ? sa : -sa);
+                acc_add(v[3], ey > 0 ? sb : -sb);
+                acc_add(v[5], ey > 0 ? sp : -sp);
+            }
+        }
+    }
+    {
+        const int per_p = (a.n_partials + gridDim.x - 1) / gridDim.x;
+        const int p0 = per_p * blockIdx.x;
+        const int p1 = p0 + per_p < a.n_partials ? p0 + per_p : a.n_partials;
+        const A *part = (const A *)a.partials;
+        for (int s = p0 + threadIdx.x; s < p1; s += LINK_THREADS) {
+#pragma unroll
+            for (int k = 0; k < CV_PARTIAL; ++k) acc_add(v[6 + k], part[CV_PARTIAL * (long long)s + k]);
+        }
+    }
+    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(v);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        A *row = (A *)a.link_partials + LINK_PARTIAL * (long long)blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) row[k] = v[k];
+        __threadfence();
+        const unsigned int ticket = atomicAdd(a.ticket, 1u);
+        last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    A w[LINK_PARTIAL];
+#pragma unroll
+    for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(w[k]);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += LINK_THREADS) {
+        const volatile A *row = (const volatile A *)a.link_partials + LINK_PARTIAL * (long long)b;
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) {
+            A r;
+            if constexpr (S == LBM_F64)
+                r = row[k];
+            else
+                r = {row[k].hi, row[k].lo};
+            acc_add(w[k], r);
+        }
+    }
+    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(w);
+    if (threadIdx.x == 0) {
+        *a.ticket = 0u;
+        double d[LINK_PARTIAL];
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) d[k] = acc_double(w[k]);
+        const long long t = *a.step_ctr;
+        // Series slot of a step: the step itself, or its parity when only the
+        // last two rows are kept.  A slot beyond the buffer (an internal
+        // invariant: the host grows the series before every launch) is not
+        // written and raises status bit 4.  The guard is a plain branch around
+        // the global stores; the stores never go through a pointer that could
+        // also refer to a thread-local array, nor is the address of the kernel
+        // parameter taken (that form lost stores in testing).
+        const bool keep_all = a.record_series != 0;
+        const long long rows = a.series_rows;
+        // DRTT(t-1) = J(t-1) - J(t) + (gained - lost)(t-1), Eq. rtt7, with
+        // J(t-1) on the post-collision state and J(t) on the pre-collision one
+        if (a.carry[4] != 0.0 && t >= 1) {
+            const long long k = keep_all ? t - 1 : ((t - 1) & 1);
+            if (k < rows) {
+                double *q = a.series + SERIES_ROW * k;
+                q[4] = (a.carry[0] - d[6]) + a.carry[2];
+                q[5] = (a.carry[1] - d[7]) + a.carry[3];
+            } else {
+                atomicOr(a.status, 4);
+            }
+        }
+        if (!a.drtt_only) {
+            const long long k = keep_all ? t : (t & 1);
+            if (k < rows) {
+                double *r = a.series + SERIES_ROW * k;
+                r[0] = d[0] + a.link_base[0];
+                r[1] = d[1] + a.link_base[1];
+                r[2] = d[2] + a.link_base[0];
+                r[3] = d[3] + a.link_base[1];
+                r[6] = d[4] + a.link_base[0];
+                r[7] = d[5] + a.link_base[1];
+                r[8] = d[6] - d[8];
+                r[9] = d[7] - d[9];
+            } else {
+                atomicOr(a.status, 4);
+            }
+            a.carry[0] = d[8];
+            a.carry[1] = d[9];
+            a.carry[2] = d[10] + a.flux_base[0];
+            a.carry[3] = d[11] + a.flux_base[1];
+            a.carry[4] = 1.0;
+            *a.step_ctr = t + 1;
+        }
+    }
+}
+
+cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st)
+{
+    const int grid = a.n_ctas;
+    switch (storage) {
+    case LBM_F64: k_link_force<LBM_F64><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    case LBM_F32: k_link_force<LBM_F32><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    case LBM_F32_DEV: k_link_force<LBM_F32_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    default: k_link_force<LBM_F16_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Read-back: pre-collision f_i(x, T) of one plane, widened to FP64 [ny][nx].
+// After a step the buffer holds ft(T-1); f(T) is its pull with bounce-back,
+// the inlet column's stored feq and the outlet copy of column nx-2.
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void k_gather(const typename Traits<S>::store_t *__restrict__ pop,
+                         const uint16_t *__restrict__ nbits, long long plane, int nx, int ny,
+                         int pitch, int periodic, int precollision, double rho0, int i,
+                         double *__restrict__ out)
+{
+    constexpr bool DEV = Traits<S>::dev;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= nx) return;
+    const long long idx = (long long)y * pitch + x;
+    double v;
+    if (nbits[idx] & 1) {
+        out[(long long)y * nx + x] = 0.0;
+        return;
+    }
+    const bool channel = !periodic;
+    if (precollision || (channel && x == 0)) {
+        v = (double)to_comp(pop[i * plane + idx]);
+    } else {
+        const int xs = (channel && x == nx - 1) ? nx - 2 : x;
+        const long long sidx = (long long)y * pitch + xs;
+        const int o = opp(i);
+        if (nbits[sidx] & (1u << o)) {
+            v = (double)to_comp(pop[o * plane + sidx]);
+        } else {
+            int sx = xs - cx(i), sy = y - cy(i);
+            if (!channel) sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            v = (double)to_comp(pop[i * plane + (long long)sy * pitch + sx]);
+        }
+    }
+    if (DEV) v += wgt<double>(i) * rho0;
+    out[(long long)y * nx + x] = v;
+}
+
+template <int S>
+__global__ void k_scatter(typename Traits<S>::store_t *__restrict__ pop,
+                          const uint16_t *__restrict__ nbits, long long plane, int nx, int ny,
+                          int pitch, double rho0, int i, const double *__restrict__ in)
+{
+    using ST = typename Traits<S>::store_t;
+    using T = typename Traits<S>::comp_t;
+    constexpr bool DEV = Traits<S>::dev;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= nx) return;
+    const long long idx = (long long)y * pitch + x;
+    double v = (nbits[idx] & 1) ? 0.0 : in[(long long)y * nx + x];
+    if (DEV && !(nbits[idx] & 1)) v -= wgt<double>(i) * rho0;
+    pop[i * plane + idx] = to_store<ST>((T)v);
+}
+
+cudaError_t launch_gather(int storage, const void *pop, const uint16_t *nbits, const void *inlet,
+                          long long plane, int nx, int ny, int pitch, int periodic,
+                          int precollision, double rho0, int plane_i, double *out,
+                          cudaStream_t st)
+{
+    (void)inlet;
+    dim3 grid((nx + 255) / 256, ny);
+    switch (storage) {
+    case LBM_F64:
+        k_gather<LBM_F64><<<grid, 256, 0, st>>>((const double *)pop, nbits, plane, nx, ny, pitch,
+                                                 periodic, precollision, rho0, plane_i, out);
+        break;
+    case LBM_F32:
+        k_gather<LBM_F32><<<grid, 256, 0, st>>>((const float *)pop, nbits, plane, nx, ny, pitch,
+                                                 periodic, precollision, rho0, plane_i, out);
+        break;
+    case LBM_F32_DEV:
+        k_gather<LBM_F32_DEV><<<grid, 256, 0, st>>>((const float *)pop, nbits, plane, nx, ny,
+                                                     pitch, periodic, precollision, rho0, plane_i,
+                                                     out);
+        break;
+    default:
+        k_gather<LBM_F16_DEV><<<grid, 256, 0, st>>>((const __half *)pop, nbits, plane, nx, ny,
+                                                     pitch, periodic, precollision, rho0, plane_i,
+                                                     out);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_pop(int storage, void *pop, const uint16_t *nbits, long long plane,
+                               int nx, int ny, int pitch, double rho0, int plane_i,
+                               const double *in, cudaStream_t st)
+{
+    dim3 grid((nx + 255) / 256, ny);
+    switch (storage) {
+    case LBM_F64:
+        k_scatter<LBM_F64><<<grid, 256, 0, st>>>((double *)pop, nbits, plane, nx, ny, pitch,
+                                                  rho0, plane_i, in);
+        break;
+    case LBM_F32:
+        k_scatter<LBM_F32><<<grid, 256, 0, st>>>((float *)pop, nbits, plane, nx, ny, pitch,
+                                                  rho0, plane_i, in);
+        break;
+    case LBM_F32_DEV:
+        k_scatter<LBM_F32_DEV><<<grid, 256, 0, st>>>((float *)pop, nbits, plane, nx, ny, pitch,
+                                                      rho0, plane_i, in);
+        break;
+    default:
+        k_scatter<LBM_F16_DEV><<<grid, 256, 0, st>>>((__half *)pop, nbits, plane, nx, ny, pitch,
+                                                      rho0, plane_i, in);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gblbm
