@@ -81,8 +81,9 @@ def measured_peaks():
 # Sources each profiled kernel is compiled from: a committed DRAM-traffic
 # figure is used only while these files are unchanged.
 KERNEL_SOURCES = {
-    "collide_stream": ["lbm_step.cu", "lbm_device.cuh", "lbm_internal.cuh"],
-    "collide_stream_f16dev": ["lbm_step.cu", "lbm_device.cuh", "lbm_internal.cuh"],
+    "collide_stream": ["lbm_step.cu", "lbm_collide.cuh", "lbm_device.cuh", "lbm_internal.cuh"],
+    "collide_stream_f16dev": ["lbm_step.cu", "lbm_collide.cuh", "lbm_device.cuh",
+                              "lbm_internal.cuh"],
     "link_force": ["lbm_link.cu", "lbm_device.cuh", "lbm_internal.cuh"],
 }
 
@@ -206,6 +207,43 @@ def variant(torch, binding, w, storage, steps, peak, device):
             "frac_of_measured_hbm": round(rl["frac"], 4)}
 
 
+def adjoint_variant(torch, binding, w, storage, steps, window, device):
+    """Wall time of lbm_adjoint (forward with checkpoints, recompute, backward,
+    gradients read back) against the forward steps alone, same start state."""
+    mask = naca_mask_device(w)
+    base = binding.Lattice(mask, w.tau, w.u_in, storage=storage, device=device)
+    f0 = base.populations()
+    base.close()
+    out = {"workload": w.name if storage == w.storage else w.name + "_as_" + storage,
+           "storage": storage, "steps": steps, "window": window,
+           "checkpoint_every": int(np.ceil(np.sqrt(steps)))}
+    for rep in range(2):  # the first pass warms allocator and graphs
+        lat = binding.Lattice(mask, w.tau, w.u_in, storage=storage, device=device)
+        lat.set_populations(f0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.step(steps)
+        lat.force_series("B", steps - window, window)
+        torch.cuda.synchronize()
+        fwd = time.perf_counter() - t0
+        lat.close()
+        lat = binding.Lattice(mask, w.tau, w.u_in, storage=storage, device=device)
+        lat.set_populations(f0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, dtau, du, df0 = lat.adjoint(steps, window, 1.0, 0.0, want_df0=True)
+        torch.cuda.synchronize()
+        adj = time.perf_counter() - t0
+        lat.close()
+    out.update({"forward_ms": round(fwd * 1e3, 2), "adjoint_ms": round(adj * 1e3, 2),
+                "adjoint_over_forward": round(adj / fwd, 2),
+                "adjoint_MLUPS": round(w.nodes * steps / adj / 1e6, 1),
+                "J": J, "dJ_dtau": dtau,
+                "includes": "forward with sqrt(N) checkpoints, segment recompute, backward "
+                            "sweep, dJ/dtau, dJ/du_in[ny], dJ/df0[9][ny][nx] read back"})
+    return out
+
+
 def oracle_sample(w, seconds, mask=None):
     """The FP64 CPU oracle on the same workload, stepped until `seconds` pass."""
     import oracle
@@ -311,13 +349,15 @@ def run_ours(a):
            "includes": "lbm_create from a pinned host mask, lbm_step(K), force series of all "
                        "four schemes read back, final populations read back, lbm_destroy"}
 
-    variants = None
+    variants = adjoint = None
     if not a.no_variants and rank == 0:
         variants = [variant(torch, binding, w, "f64", 1000, peak, local),
                     variant(torch, binding, w, "f32dev", 4000, peak, local),
                     variant(torch, binding, w, "f16dev", 4000, peak, local),
                     variant(torch, binding, inputs.PRECISION, "f16dev", 2000, peak, local),
                     variant(torch, binding, inputs.PRECISION, "f32dev", 1000, peak, local)]
+        adjoint = [adjoint_variant(torch, binding, inputs.DIFF, "f32", 4000, 1000, local),
+                   adjoint_variant(torch, binding, w, "f32", 1000, 500, local)]
 
     cpu = None
     if rank == 0 and world == 1:
@@ -351,6 +391,7 @@ def run_ours(a):
             "gpu_launches": int(launches),
             "clocks": clk,
             "variants": variants,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -12,6 +12,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "lbm_host.h"
 #include "lbm_internal.cuh"
 
 using namespace gblbm;
@@ -133,110 +134,6 @@ void dev_free(lbm_ctx *h, void *p)
         cudaFree(p);
 }
 
-size_t storage_bytes(int storage)
-{
-    switch (storage) {
-    case LBM_F64: return 8;
-    case LBM_F16_DEV: return 2;
-    default: return 4;
-    }
-}
-
-// Default control volume; the same rule is stated in gblbm.h.
-void auto_cv(const uint8_t *mask, int nx, int ny, int periodic, int *cv)
-{
-    int xmin = nx, xmax = -1, ymin = ny, ymax = -1;
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x)
-            if (mask[(size_t)y * nx + x]) {
-                xmin = x < xmin ? x : xmin;
-                xmax = x > xmax ? x : xmax;
-                ymin = y < ymin ? y : ymin;
-                ymax = y > ymax ? y : ymax;
-            }
-    if (xmax < 0) {
-        cv[0] = periodic ? 0 : 1;
-        cv[1] = periodic ? nx - 1 : nx - 2;
-        cv[2] = 0;
-        cv[3] = ny - 1;
-        return;
-    }
-    int m = (xmax - xmin + 1 + 3) / 4;
-    if (m < 4) m = 4;
-    int x0 = xmin - m, x1 = xmax + m, y0 = ymin - m, y1 = ymax + m;
-    if (periodic) {
-        if (x0 < 1 || x1 > nx - 2) {
-            x0 = 0;
-            x1 = nx - 1;
-        }
-    } else {
-        x0 = x0 < 1 ? 1 : x0;
-        x1 = x1 > nx - 2 ? nx - 2 : x1;
-    }
-    if (y0 < 1 || y1 > ny - 2) {
-        y0 = 0;
-        y1 = ny - 1;
-    }
-    cv[0] = x0;
-    cv[1] = x1;
-    cv[2] = y0;
-    cv[3] = y1;
-}
-
-// Fixed momentum of the deviation base w_i rho0 (geometry only):
-//   link_base = 2 rho0 sum over links (x_f, i) of c_i w_i (each link's
-//   populations f_i and f_opp carry w_i rho0 each; so does the bounced ft_i);
-//   flux_base = rho0 sum over box-surface crossings of +-c_i w_i.
-// Links are enumerated from the solid nodes, crossings from the box edge.
-void base_sums(const uint8_t *mask, int nx, int ny, int periodic, const int *cv, double rho0,
-               double *link_base, double *flux_base)
-{
-    const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    auto W = [](int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); };
-    auto solid = [&](int x, int y) { return mask[(size_t)y * nx + x] != 0; };
-    auto wrap = [&](int &x, int &y) {
-        y = (y % ny + ny) % ny;
-        if (x < 0 || x >= nx) {
-            if (!periodic) return false;
-            x = (x % nx + nx) % nx;
-        }
-        return true;
-    };
-    double lb[2] = {0, 0};
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-            if (!solid(x, y)) continue;
-            for (int i = 1; i < 9; ++i) {  // fluid x_f = s - c_i with x_f + c_i = s
-                int xf = x - CX[i], yf = y - CY[i];
-                if (!wrap(xf, yf) || solid(xf, yf)) continue;
-                lb[0] += CX[i] * W(i);
-                lb[1] += CY[i] * W(i);
-            }
-        }
-    double fb[2] = {0, 0};
-    auto inbox = [&](int x, int y) { return x >= cv[0] && x <= cv[1] && y >= cv[2] && y <= cv[3]; };
-    for (int y = cv[2] - 1; y <= cv[3] + 1; ++y)
-        for (int x = cv[0] - 1; x <= cv[1] + 1; ++x) {
-            int xn = x, yn = y;
-            if (!wrap(xn, yn)) continue;
-            if (x != xn || y != yn) continue;  // each node once, in unwrapped position
-            if (solid(xn, yn)) continue;
-            const bool in = inbox(xn, yn);
-            for (int i = 1; i < 9; ++i) {
-                int x2 = xn + CX[i], y2 = yn + CY[i];
-                if (!wrap(x2, y2) || solid(x2, y2) || inbox(x2, y2) == in) continue;
-                const double s = in ? -1.0 : 1.0;
-                fb[0] += s * CX[i] * W(i);
-                fb[1] += s * CY[i] * W(i);
-            }
-        }
-    link_base[0] = 2.0 * rho0 * lb[0];
-    link_base[1] = 2.0 * rho0 * lb[1];
-    flux_base[0] = rho0 * fb[0];
-    flux_base[1] = rho0 * fb[1];
-}
-
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -275,13 +172,6 @@ bool encode_tensor_map(CUtensorMap *m, int storage, void *base, int pitch, int n
     return enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-bool range_ok(int lo, int hi, int n, bool whole_allowed)
-{
-    if (lo > hi) return false;
-    if (lo >= 1 && hi <= n - 2) return true;
-    return whole_allowed && lo == 0 && hi == n - 1;
 }
 
 int next_buf(int b) { return b + 1 == NBUF ? 0 : b + 1; }
@@ -506,13 +396,6 @@ void free_all(lbm_ctx *h)
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
-bool finite_all(const double *v, int n)
-{
-    for (int i = 0; i < n; ++i)
-        if (!std::isfinite(v[i])) return false;
-    return true;
-}
-
 }  // namespace
 
 extern "C" {
@@ -538,15 +421,6 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
         bc = *bc_in;
     else
         lbm_bc_default(&bc);
-    if (!mask || !u_in) return set_err(nullptr, LBM_EINVAL, "mask and u_in must not be NULL");
-    if (nx < 4 || ny < 3) return set_err(nullptr, LBM_EINVAL, "grid %dx%d too small (nx >= 4, ny >= 3)", nx, ny);
-    if ((long long)nx * ny * 8 >= (1LL << 31))
-        return set_err(nullptr, LBM_EINVAL, "grid %dx%d too large for int32 link indices", nx, ny);
-    if (!(tau > 0.5) || !std::isfinite(tau))
-        return set_err(nullptr, LBM_EINVAL, "tau must be finite and > 0.5 (got %g)", tau);
-    if (n_u_in != 1 && n_u_in != ny)
-        return set_err(nullptr, LBM_EINVAL, "n_u_in must be 1 or ny (got %d)", n_u_in);
-    if (!finite_all(u_in, n_u_in)) return set_err(nullptr, LBM_EINVAL, "u_in is not finite");
     if (bc.kernel != 0 && bc.kernel != 1)
         return set_err(nullptr, LBM_EINVAL, "unknown kernel choice %d", bc.kernel);
     if (bc.kind != LBM_BC_CHANNEL && bc.kind != LBM_BC_PERIODIC)
@@ -559,24 +433,10 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if ((bc.alloc == nullptr) != (bc.free == nullptr))
         return set_err(nullptr, LBM_EINVAL, "alloc and free must be given together");
     const int periodic = bc.kind == LBM_BC_PERIODIC;
-    if (!periodic) {
-        const int cols[4] = {0, 1, nx - 2, nx - 1};
-        for (int y = 0; y < ny; ++y)
-            for (int c : cols)
-                if (mask[(size_t)y * nx + c])
-                    return set_err(nullptr, LBM_EINVAL,
-                                   "solid node at (%d, %d): columns 0, 1, nx-2, nx-1 of a channel must be fluid",
-                                   c, y);
-    }
     int cv[4];
-    if (bc.cv[0] < 0) {
-        auto_cv(mask, nx, ny, periodic, cv);
-    } else {
-        memcpy(cv, bc.cv, sizeof(cv));
-        if (!range_ok(cv[0], cv[1], nx, periodic != 0) || !range_ok(cv[2], cv[3], ny, true))
-            return set_err(nullptr, LBM_EINVAL,
-                           "control volume {%d,%d,%d,%d} must lie within [1, n-2] (or span a periodic direction)",
-                           cv[0], cv[1], cv[2], cv[3]);
+    {
+        const std::string why = check_domain(mask, nx, ny, tau, u_in, n_u_in, periodic, bc.cv, cv);
+        if (!why.empty()) return set_err(nullptr, LBM_EINVAL, "%s", why.c_str());
     }
     int ndev = 0;
     cudaError_t de = cudaGetDeviceCount(&ndev);
@@ -617,15 +477,8 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     h->plane = (long long)ny * h->pitch;
     h->tiles_x = (nx + TILE_X - 1) / TILE_X;
     h->tiles_y = (ny + tile_rows(h->storage) - 1) / tile_rows(h->storage);
-    {
-        int hx0 = cv[0] - 1 < 0 ? 0 : cv[0] - 1, hx1 = cv[1] + 1 > nx - 1 ? nx - 1 : cv[1] + 1;
-        int hy0 = cv[2] - 1 < 0 ? 0 : cv[2] - 1, hy1 = cv[3] + 1 > ny - 1 ? ny - 1 : cv[3] + 1;
-        h->cvt[0] = hx0 / TILE_X;
-        h->cvt[1] = hx1 / TILE_X;
-        h->cvt[2] = hy0 / tile_rows(h->storage);
-        h->cvt[3] = hy1 / tile_rows(h->storage);
-        h->n_cv_tiles = (h->cvt[1] - h->cvt[0] + 1) * (h->cvt[3] - h->cvt[2] + 1);
-    }
+    cv_tile_rect(cv, nx, ny, TILE_X, tile_rows(h->storage), h->cvt);
+    h->n_cv_tiles = (h->cvt[1] - h->cvt[0] + 1) * (h->cvt[3] - h->cvt[2] + 1);
     if (bc.cuda_stream) {
         h->stream = (cudaStream_t)bc.cuda_stream;
     } else {
