@@ -256,6 +256,108 @@ const char *lbm_last_error(const lbm_ctx *h);
 /* Release the handle and its device memory.  NULL is ignored. */
 void lbm_destroy(lbm_ctx *h);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent domains advanced together.
+ *
+ * A batch holds n domains.  Each is a full problem of its own, as lbm_create
+ * defines one: its own grid, body mask, relaxation time, inlet profile and
+ * control volume.  They share one boundary kind, storage type and rho0.  One
+ * batch step advances every domain by one time step.  It does that in one
+ * collide-stream launch over a table of the tiles of all domains, followed
+ * by one link launch (one CTA per domain).  Steps are replayed from captured
+ * CUDA graphs.  Per domain, the arithmetic and the force rows equal those of
+ * a single-domain handle; only the summation order of the DRTT box sums
+ * depends on the tile shape.
+ * The paper treats one body at a time; the batch serves sweeps of its
+ * Section V airfoil study (angle of attack, thickness, Reynolds number) in
+ * one launch.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+/* One domain: the arguments of lbm_create for it (all host memory, read
+ * during lbm_batch_create only). */
+typedef struct {
+    const uint8_t *mask;  /* uint8 [ny][nx], nonzero = solid */
+    int nx, ny;
+    double tau;           /* > 0.5 */
+    const double *u_in;   /* n_u_in values: 1 (uniform) or ny (per row) */
+    int n_u_in;
+    int cv[4];            /* control volume x0, x1, y0, y1 inclusive; cv[0] < 0: default */
+} lbm_domain;
+
+/* Create a batch of n >= 1 domains.  bc gives the boundary kind, storage,
+ * rho0, stream and allocator of all domains (bc->cv is ignored: each domain
+ * has its own).  The body force must be zero and bc->kernel 0.  The force
+ * series is always kept in full when bc->record_series is 1; otherwise only
+ * the last two steps are kept.  Initial state as lbm_create.  The launch
+ * configuration starts at tile shape 0 with one CTA per tile;
+ * lbm_batch_autotune picks a faster one.
+ * EINVAL: n < 1, any domain failing lbm_create's checks (the message names
+ * the domain), a nonzero body force, bc->kernel != 0.  ENOMEM / ECUDA as named. */
+lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc, lbm_batch **out);
+
+/* Advance every domain n >= 0 steps (as lbm_step, for each domain).
+ * Blocks until the work is done.  EUNSTABLE when any domain's instability
+ * flag is set (the flags are sticky; lbm_batch_status names the domains);
+ * every domain has still taken all n steps.  ESTATE if a series row would
+ * have fallen outside the series buffer (an internal invariant). */
+lbm_status lbm_batch_step(lbm_batch *b, int n);
+
+/* Forces of every domain at one step (0 <= step < steps done), for a scheme
+ * of lbm_scheme: fx[n], fy[n].  As lbm_force_series for each domain. */
+lbm_status lbm_batch_forces(lbm_batch *b, int scheme, long step, double *fx, double *fy);
+
+/* Force series of one domain, steps [first, first+count): as lbm_force_series. */
+lbm_status lbm_batch_force_series(lbm_batch *b, int domain, int scheme, long first, long count,
+                                  double *fx, double *fy);
+
+/* Pre-collision populations of one domain at the current step: out is double
+ * [9][ny][nx] of that domain (0 at solid nodes), as lbm_populations. */
+lbm_status lbm_batch_populations(lbm_batch *b, int domain, double *out);
+
+/* Set the pre-collision populations of one domain, before the first step
+ * only (ESTATE afterwards): in is double [9][ny][nx], finite. */
+lbm_status lbm_batch_set_populations(lbm_batch *b, int domain, const double *in);
+
+/* Per-domain instability flags: unstable[d] = 1 when domain d produced
+ * rho <= 0 or NaN in some step, and first_bad_step[d] = that step (-1 when
+ * the flag is clear).  Either pointer may be NULL. */
+lbm_status lbm_batch_status(lbm_batch *b, int *unstable, long *first_bad_step);
+
+/* Launch configuration of the batched collide-stream kernel.
+ * shape: a tile shape index (0 .. lbm_batch_num_shapes()-1).
+ * ctas_per_sm: 0 for one CTA per tile, k > 0 for a persistent grid of
+ * k * (SM count) CTAs walking the tile table.  Shapes and grids differ only
+ * in speed and in the summation order of the DRTT box sums.
+ * EINVAL: an unknown shape, or k above what the SM can hold of that kernel. */
+lbm_status lbm_batch_set_launch(lbm_batch *b, int shape, int ctas_per_sm);
+lbm_status lbm_batch_get_launch(const lbm_batch *b, int *shape, int *ctas_per_sm);
+
+/* Tile shape k: width tile_w nodes along x by tile_h rows, for the batch's
+ * storage type (EINVAL for an unknown k). */
+int lbm_batch_num_shapes(void);
+lbm_status lbm_batch_shape(const lbm_batch *b, int k, int *tile_w, int *tile_h);
+
+/* Time every tile shape with every grid the SM can hold (one CTA per tile,
+ * or 1, 2, 3, 4, 6, 8 CTAs per SM), trials launches each after one warm-up,
+ * and keep the fastest.  The trials run the collide-stream kernel alone,
+ * from the current state into the spare buffer.  Their partial sums and
+ * flags go to scratch memory, so the simulation state and its results do
+ * not change.  On return *shape and *ctas_per_sm (either may be NULL) hold
+ * the choice, and *best_ms its time per launch. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int trials, int *shape, int *ctas_per_sm,
+                              double *best_ms);
+
+long lbm_batch_steps_done(const lbm_batch *b);
+int lbm_batch_num_domains(const lbm_batch *b);
+/* Total nodes of all domains (the unit of the batch's MLUPS). */
+long long lbm_batch_nodes(const lbm_batch *b);
+/* Kernel launches issued by the batch so far (set-up included). */
+long long lbm_batch_launch_count(const lbm_batch *b);
+/* Message of the last failed call on b (or of the calling thread when b is NULL). */
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

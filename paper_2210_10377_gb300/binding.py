@@ -40,6 +40,12 @@ class lbm_bc(C.Structure):
                 ("kernel", C.c_int)]
 
 
+class lbm_domain(C.Structure):
+    _fields_ = [("mask", C.POINTER(C.c_uint8)), ("nx", C.c_int), ("ny", C.c_int),
+                ("tau", C.c_double), ("u_in", C.POINTER(C.c_double)), ("n_u_in", C.c_int),
+                ("cv", C.c_int * 4)]
+
+
 _lib = None
 
 
@@ -82,6 +88,37 @@ def lib():
     for name in ("lbm_create", "lbm_step", "lbm_force", "lbm_force_series", "lbm_populations",
                  "lbm_set_populations", "lbm_links", "lbm_control_volume", "lbm_naca_mask",
                  "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_adjoint"):
+        getattr(L, name).restype = C.c_int
+    # batches
+    L.lbm_batch_create.argtypes = [C.POINTER(lbm_domain), C.c_int, C.POINTER(lbm_bc), C.POINTER(vp)]
+    L.lbm_batch_step.argtypes = [vp, C.c_int]
+    L.lbm_batch_forces.argtypes = [vp, C.c_int, C.c_long, dp, dp]
+    L.lbm_batch_force_series.argtypes = [vp, C.c_int, C.c_int, C.c_long, C.c_long, dp, dp]
+    L.lbm_batch_populations.argtypes = [vp, C.c_int, dp]
+    L.lbm_batch_set_populations.argtypes = [vp, C.c_int, dp]
+    L.lbm_batch_status.argtypes = [vp, ip, lp]
+    L.lbm_batch_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    L.lbm_batch_get_launch.argtypes = [vp, ip, ip]
+    L.lbm_batch_num_shapes.argtypes = []
+    L.lbm_batch_num_shapes.restype = C.c_int
+    L.lbm_batch_shape.argtypes = [vp, C.c_int, ip, ip]
+    L.lbm_batch_autotune.argtypes = [vp, C.c_int, ip, ip, dp]
+    L.lbm_batch_steps_done.argtypes = [vp]
+    L.lbm_batch_steps_done.restype = C.c_long
+    L.lbm_batch_num_domains.argtypes = [vp]
+    L.lbm_batch_num_domains.restype = C.c_int
+    L.lbm_batch_nodes.argtypes = [vp]
+    L.lbm_batch_nodes.restype = C.c_longlong
+    L.lbm_batch_launch_count.argtypes = [vp]
+    L.lbm_batch_launch_count.restype = C.c_longlong
+    L.lbm_batch_last_error.argtypes = [vp]
+    L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
+    for name in ("lbm_batch_create", "lbm_batch_step", "lbm_batch_forces", "lbm_batch_force_series",
+                 "lbm_batch_populations", "lbm_batch_set_populations", "lbm_batch_status",
+                 "lbm_batch_set_launch", "lbm_batch_get_launch", "lbm_batch_shape",
+                 "lbm_batch_autotune"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -267,3 +304,145 @@ class Lattice:
         n = (C.c_long * 2)()
         _check(lib().lbm_kernel_times(self._h, ms, n, int(bool(reset))), self._h)
         return {"collide_stream": (ms[0], n[0]), "link_force": (ms[1], n[1])}
+
+
+def _bcheck(rc, b=None):
+    if rc != 0:
+        msg = lib().lbm_batch_last_error(b)
+        raise LbmError(rc, msg.decode() if msg else "")
+
+
+class Batch:
+    """Many independent domains stepped together (lbm_batch_create ... destroy).
+
+    domains: a list of dicts with keys mask (uint8 [ny][nx]), tau, u_in (scalar
+    or ny values) and optionally cv (4 ints)."""
+
+    def __init__(self, domains, *, kind=CHANNEL, storage="f32", rho0=1.0, record_series=True,
+                 stream=None, torch_alloc=True, device=0):
+        import torch
+        L = lib()
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        self._keep = []
+        arr = (lbm_domain * len(domains))()
+        self.shapes = []
+        for k, d in enumerate(domains):
+            m = np.ascontiguousarray(d["mask"], np.uint8)
+            u = np.ascontiguousarray(np.atleast_1d(np.asarray(d["u_in"], np.float64)))
+            self._keep += [m, u]
+            arr[k].mask = m.ctypes.data_as(C.POINTER(C.c_uint8))
+            arr[k].ny, arr[k].nx = m.shape
+            arr[k].tau = float(d["tau"])
+            arr[k].u_in = _dp(u)
+            arr[k].n_u_in = int(u.size)
+            cv = d.get("cv")
+            for j in range(4):
+                arr[k].cv[j] = int(cv[j]) if cv is not None else -1
+            self.shapes.append(m.shape)
+        bc = lbm_bc()
+        L.lbm_bc_default(C.byref(bc))
+        bc.kind = int(kind)
+        bc.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        bc.rho0 = float(rho0)
+        bc.record_series = int(bool(record_series))
+        bc.cuda_stream = self.stream.cuda_stream
+        self._alloc = _TorchAllocator(device) if torch_alloc else None
+        if self._alloc is not None:
+            bc.alloc = self._alloc.alloc
+            bc.free = self._alloc.free
+        self.storage = bc.storage
+        h = C.c_void_p()
+        with torch.cuda.device(device):
+            _bcheck(L.lbm_batch_create(arr, len(domains), C.byref(bc), C.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        _bcheck(lib().lbm_batch_step(self._h, int(n)), self._h)
+
+    def forces(self, scheme, step=None):
+        """(fx[n], fy[n]) of every domain at one step (default: the last)."""
+        n = self.num_domains
+        step = self.steps_done - 1 if step is None else int(step)
+        fx, fy = np.zeros(n), np.zeros(n)
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        _bcheck(lib().lbm_batch_forces(self._h, sc, step, _dp(fx), _dp(fy)), self._h)
+        return fx, fy
+
+    def force_series(self, domain, scheme, first=0, count=None):
+        if count is None:
+            count = self.steps_done - first
+        fx, fy = np.zeros(count), np.zeros(count)
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        _bcheck(lib().lbm_batch_force_series(self._h, int(domain), sc, int(first), int(count),
+                                             _dp(fx), _dp(fy)), self._h)
+        return fx, fy
+
+    def populations(self, domain):
+        ny, nx = self.shapes[domain]
+        out = np.zeros((9, ny, nx))
+        _bcheck(lib().lbm_batch_populations(self._h, int(domain), _dp(out)), self._h)
+        return out
+
+    def set_populations(self, domain, f):
+        f = np.ascontiguousarray(f, np.float64)
+        _bcheck(lib().lbm_batch_set_populations(self._h, int(domain), _dp(f)), self._h)
+
+    def status(self):
+        n = self.num_domains
+        flags = (C.c_int * n)()
+        first = (C.c_long * n)()
+        _bcheck(lib().lbm_batch_status(self._h, flags, first), self._h)
+        return np.array(flags[:], np.int32), np.array(first[:], np.int64)
+
+    def set_launch(self, shape, ctas_per_sm):
+        _bcheck(lib().lbm_batch_set_launch(self._h, int(shape), int(ctas_per_sm)), self._h)
+
+    def launch(self):
+        s, k = C.c_int(), C.c_int()
+        _bcheck(lib().lbm_batch_get_launch(self._h, C.byref(s), C.byref(k)), self._h)
+        return s.value, k.value
+
+    def shape(self, k):
+        w, h = C.c_int(), C.c_int()
+        _bcheck(lib().lbm_batch_shape(self._h, int(k), C.byref(w), C.byref(h)), self._h)
+        return w.value, h.value
+
+    def autotune(self, trials=5):
+        """Time every (tile shape, grid) and keep the fastest: (shape, ctas_per_sm, ms)."""
+        s, k, ms = C.c_int(), C.c_int(), C.c_double()
+        _bcheck(lib().lbm_batch_autotune(self._h, int(trials), C.byref(s), C.byref(k), C.byref(ms)),
+                self._h)
+        return s.value, k.value, ms.value
+
+    @property
+    def num_shapes(self):
+        return lib().lbm_batch_num_shapes()
+
+    @property
+    def steps_done(self):
+        return lib().lbm_batch_steps_done(self._h)
+
+    @property
+    def num_domains(self):
+        return lib().lbm_batch_num_domains(self._h)
+
+    @property
+    def nodes(self):
+        return lib().lbm_batch_nodes(self._h)
+
+    @property
+    def launch_count(self):
+        return lib().lbm_batch_launch_count(self._h)

@@ -568,7 +568,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     CKC(cudaMemcpyAsync(h->u_row, urow.data(), sizeof(double) * ny, cudaMemcpyHostToDevice, s), "H2D u_in");
     CKC(launch_node_bits(h->mask_d, h->nbits, nx, ny, h->pitch, periodic, s), "node bits");
     CKC(launch_tile_flags(h->nbits, nx, ny, h->pitch, periodic, h->tile_flag, h->tiles_x, h->tiles_y,
-                          tile_rows(h->storage), s),
+                          TILE_X, tile_rows(h->storage), s),
         "tile flags");
     // link list: count, scan, scatter
     const int nb = link_blocks(nx, ny);

@@ -160,8 +160,9 @@ cudaError_t launch_scan_blocks(int *block_cnt, int nblocks, long long *total, cu
 cudaError_t launch_link_scatter(const uint16_t *nbits, int nx, int ny, int pitch,
                                 const int *block_off, int32_t *links, long long cap,
                                 cudaStream_t st);
+// tw x rows tiles (tw <= 1024)
 cudaError_t launch_tile_flags(const uint16_t *nbits, int nx, int ny, int pitch, int periodic,
-                              uint8_t *flags, int tiles_x, int tiles_y, int rows,
+                              uint8_t *flags, int tiles_x, int tiles_y, int tw, int rows,
                               cudaStream_t st);
 int link_blocks(int nx, int ny);
 

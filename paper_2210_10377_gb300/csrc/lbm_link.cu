@@ -4,20 +4,126 @@
 //   exchange of step t for algorithms A, A' and B (Eqs. MEA, rtt4, rtt5), fold
 //   the control-volume partials into J(t), and the last CTA to finish completes
 //   DRTT(t-1) = J(t-1) - J(t) + GL(t-1) (Eq. rtt7).
+// k_link_force_batch: the same for every domain of a batch, one CTA each.
 // k_gather / k_scatter: one population plane between the device storage and
 //   an FP64 [ny][nx] array (pre-collision f(x, T) reconstructed by a pull).
 //
 // Reductions are deterministic (fixed trees, no floating-point atomics).
+#include "lbm_batch.cuh"
 #include "lbm_device.cuh"
 
 namespace gblbm {
 
 // ---------------------------------------------------------------------------
-// Link force + finalisation.  n_ctas CTAs of LINK_THREADS threads share the
-// links (contiguous chunks) and the control-volume partials; each writes one
-// partial row.  The last CTA to finish (atomic ticket) sums the rows in slot
-// order, so the result does not depend on which CTA finishes last, and
-// completes the step's series row and the DRTT of the previous step.
+// Per-link momentum exchange of step t over links [k0, k1) and the sum of the
+// control-volume partial rows [p0, p1) (Eqs. MEA, rtt4, rtt5, rtt7):
+// v: A(2), B(2), A'(2), J_pre(2), J_post(2), GL(2).
+// ---------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ void link_sums(const LinkArgs &a, long long k0, long long k1, int p0, int p1,
+                                          typename AccOf<S>::type (&v)[LINK_PARTIAL])
+{
+    using ST = typename Traits<S>::store_t;
+    using T = typename Traits<S>::comp_t;
+    using A = typename AccOf<S>::type;
+    const ST *__restrict__ src = (const ST *)a.src;
+    const ST *__restrict__ dst = (const ST *)a.dst;
+    const long long plane = a.plane;
+#pragma unroll
+    for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(v[k]);
+    for (long long k = k0 + threadIdx.x; k < k1; k += LINK_THREADS) {
+        const int l = a.links[k];
+        const int n = l >> 3;
+        const int i = (l & 7) + 1;
+        const int o = opp(i);
+        const int x = n % a.nx, y = n / a.nx;
+        const long long idx = (long long)y * a.pitch + x;
+        T fi, fo;
+        if (a.precollision) {
+            fi = to_comp(src[i * plane + idx]);
+            fo = to_comp(src[o * plane + idx]);
+        } else {
+            // f_i(x_f, t): pulled from x_f - c_i, or bounced when that node is solid
+            if (a.nbits[idx] & (1u << o)) {
+                fi = to_comp(src[o * plane + idx]);
+            } else {
+                int sx = x - cx(i), sy = y - cy(i);
+                if (a.periodic) sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+                sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+                fi = to_comp(src[i * plane + (long long)sy * a.pitch + sx]);
+            }
+            // f_opp(i)(x_f, t): x_f + c_i is solid, so it is the bounced ft_i(x_f, t-1)
+            fo = to_comp(src[i * plane + idx]);
+        }
+        const T ft = to_comp(dst[i * plane + idx]);
+        A sa, sb, sp;
+        if constexpr (S == LBM_F64) {
+            sa = fi + fo;
+            sb = 2.0 * ft;
+            sp = fi + ft;
+        } else {
+            sa = ff_two_sum(fi, fo);
+            sb = {2.0f * ft, 0.0f};
+            sp = ff_two_sum(fi, ft);
+        }
+        const int ex = cx(i), ey = cy(i);
+        if (ex != 0) {
+            acc_add(v[0], ex > 0 ? sa : -sa);
+            acc_add(v[2], ex > 0 ? sb : -sb);
+            acc_add(v[4], ex > 0 ? sp : -sp);
+        }
+        if (ey != 0) {
+            acc_add(v[1], ey > 0 ? sa : -sa);
+            acc_add(v[3], ey > 0 ? sb : -sb);
+            acc_add(v[5], ey > 0 ? sp : -sp);
+        }
+    }
+    const A *part = (const A *)a.partials;
+    for (int s = p0 + threadIdx.x; s < p1; s += LINK_THREADS) {
+#pragma unroll
+        for (int k = 0; k < CV_PARTIAL; ++k) acc_add(v[6 + k], part[CV_PARTIAL * (long long)s + k]);
+    }
+}
+
+// Completes the force rows from the reduced sums d (one thread).  prev: the
+// row of step t-1, which receives DRTT(t-1) = J(t-1) - J(t) + (gained -
+// lost)(t-1) (Eq. rtt7, J(t-1) on the post-collision state, J(t) on the
+// pre-collision one); cur: the row of step t (A, B, A', defect), written and
+// the carry advanced unless drtt_only.  A null row pointer skips that row's
+// stores: the callers guard their row slots with plain branches, and no row
+// pointer may refer to a thread-local array (that form lost stores).
+__device__ __forceinline__ void finish_rows(const LinkArgs &a, const double (&d)[LINK_PARTIAL], long long t,
+                                            double *prev, double *cur, bool drtt_only)
+{
+    if (prev && a.carry[4] != 0.0 && t >= 1) {
+        prev[4] = (a.carry[0] - d[6]) + a.carry[2];
+        prev[5] = (a.carry[1] - d[7]) + a.carry[3];
+    }
+    if (drtt_only) return;
+    if (cur) {
+        cur[0] = d[0] + a.link_base[0];
+        cur[1] = d[1] + a.link_base[1];
+        cur[2] = d[2] + a.link_base[0];
+        cur[3] = d[3] + a.link_base[1];
+        cur[6] = d[4] + a.link_base[0];
+        cur[7] = d[5] + a.link_base[1];
+        cur[8] = d[6] - d[8];
+        cur[9] = d[7] - d[9];
+    }
+    a.carry[0] = d[8];
+    a.carry[1] = d[9];
+    a.carry[2] = d[10] + a.flux_base[0];
+    a.carry[3] = d[11] + a.flux_base[1];
+    a.carry[4] = 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Link force + finalisation of one domain.  n_ctas CTAs of LINK_THREADS
+// threads share the links (contiguous chunks) and the control-volume
+// partials; each writes one partial row.  The last CTA to finish (atomic
+// ticket) sums the rows in slot order, so the result does not depend on which
+// CTA finishes last, and completes the step's series row and the DRTT of the
+// previous step.
 // Series row t: A(2) B(2) DRTT(2) A'(2) defect(2), where defect is the
 // collision's momentum defect inside the box, J_pre(t) - J_post(t).
 // For deviation storage the momentum of the base w_i rho0 over the links and
@@ -27,77 +133,17 @@ namespace gblbm {
 template <int S>
 __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
 {
-    using ST = typename Traits<S>::store_t;
-    using T = typename Traits<S>::comp_t;
     using A = typename AccOf<S>::type;
-    const ST *__restrict__ src = (const ST *)a.src;
-    const ST *__restrict__ dst = (const ST *)a.dst;
-    const long long plane = a.plane;
-    // v: A(2), B(2), A'(2), J_pre(2), J_post(2), GL(2)
     A v[LINK_PARTIAL];
-#pragma unroll
-    for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(v[k]);
-    const long long per = (a.nlinks + gridDim.x - 1) / gridDim.x;
-    const long long k0 = per * blockIdx.x;
-    const long long k1 = k0 + per < a.nlinks ? k0 + per : a.nlinks;
-    if (!a.drtt_only) {
-        for (long long k = k0 + threadIdx.x; k < k1; k += LINK_THREADS) {
-            const int l = a.links[k];
-            const int n = l >> 3;
-            const int i = (l & 7) + 1;
-            const int o = opp(i);
-            const int x = n % a.nx, y = n / a.nx;
-            const long long idx = (long long)y * a.pitch + x;
-            T fi, fo;
-            if (a.precollision) {
-                fi = to_comp(src[i * plane + idx]);
-                fo = to_comp(src[o * plane + idx]);
-            } else {
-                // f_i(x_f, t): pulled from x_f - c_i, or bounced when that node is solid
-                if (a.nbits[idx] & (1u << o)) {
-                    fi = to_comp(src[o * plane + idx]);
-                } else {
-                    int sx = x - cx(i), sy = y - cy(i);
-                    if (a.periodic) sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-                    sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
-                    fi = to_comp(src[i * plane + (long long)sy * a.pitch + sx]);
-                }
-                // f_opp(i)(x_f, t): x_f + c_i is solid, so it is the bounced ft_i(x_f, t-1)
-                fo = to_comp(src[i * plane + idx]);
-            }
-            const T ft = to_comp(dst[i * plane + idx]);
-            A sa, sb, sp;
-            if constexpr (S == LBM_F64) {
-                sa = fi + fo;
-                sb = 2.0 * ft;
-                sp = fi + ft;
-            } else {
-                sa = ff_two_sum(fi, fo);
-                sb = {2.0f * ft, 0.0f};
-                sp = ff_two_sum(fi, ft);
-            }
-            const int ex = cx(i), ey = cy(i);
-            if (ex != 0) {
-                acc_add(v[0], ex > 0 ? sa : -sa);
-                acc_add(v[2], ex > 0 ? sb : -sb);
-                acc_add(v[4], ex > 0 ? sp : -sp);
-            }
-            if (ey != 0) {
-                acc_add(v[1], ey > 0 ? sa : -sa);
-                acc_add(v[3], ey > 0 ? sb : -sb);
-                acc_add(v[5], ey > 0 ? sp : -sp);
-            }
-        }
-    }
     {
+        const long long nl = a.drtt_only ? 0 : a.nlinks;
+        const long long per = (nl + gridDim.x - 1) / gridDim.x;
+        const long long k0 = per * blockIdx.x;
+        const long long k1 = k0 + per < nl ? k0 + per : nl;
         const int per_p = (a.n_partials + gridDim.x - 1) / gridDim.x;
         const int p0 = per_p * blockIdx.x;
         const int p1 = p0 + per_p < a.n_partials ? p0 + per_p : a.n_partials;
-        const A *part = (const A *)a.partials;
-        for (int s = p0 + threadIdx.x; s < p1; s += LINK_THREADS) {
-#pragma unroll
-            for (int k = 0; k < CV_PARTIAL; ++k) acc_add(v[6 + k], part[CV_PARTIAL * (long long)s + k]);
-        }
+        link_sums<S>(a, k0, k1 > k0 ? k1 : k0, p0, p1 > p0 ? p1 : p0, v);
     }
     block_reduce<A, LINK_PARTIAL, LINK_THREADS>(v);
     __shared__ bool last;
@@ -137,46 +183,24 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
         // Series slot of a step: the step itself, or its parity when only the
         // last two rows are kept.  A slot beyond the buffer (an internal
         // invariant: the host grows the series before every launch) is not
-        // written and raises status bit 4.  The guard is a plain branch around
-        // the global stores; the stores never go through a pointer that could
-        // also refer to a thread-local array, nor is the address of the kernel
-        // parameter taken (that form lost stores in testing).
+        // written and raises status bit 4.
         const bool keep_all = a.record_series != 0;
-        const long long rows = a.series_rows;
-        // DRTT(t-1) = J(t-1) - J(t) + (gained - lost)(t-1), Eq. rtt7, with
-        // J(t-1) on the post-collision state and J(t) on the pre-collision one
-        if (a.carry[4] != 0.0 && t >= 1) {
-            const long long k = keep_all ? t - 1 : ((t - 1) & 1);
-            if (k < rows) {
-                double *q = a.series + SERIES_ROW * k;
-                q[4] = (a.carry[0] - d[6]) + a.carry[2];
-                q[5] = (a.carry[1] - d[7]) + a.carry[3];
-            } else {
+        const long long kp = keep_all ? t - 1 : ((t - 1) & 1), kc = keep_all ? t : (t & 1);
+        double *prev = nullptr, *cur = nullptr;
+        if (t >= 1 && a.carry[4] != 0.0) {
+            if (kp < a.series_rows)
+                prev = a.series + SERIES_ROW * kp;
+            else
                 atomicOr(a.status, 4);
-            }
         }
         if (!a.drtt_only) {
-            const long long k = keep_all ? t : (t & 1);
-            if (k < rows) {
-                double *r = a.series + SERIES_ROW * k;
-                r[0] = d[0] + a.link_base[0];
-                r[1] = d[1] + a.link_base[1];
-                r[2] = d[2] + a.link_base[0];
-                r[3] = d[3] + a.link_base[1];
-                r[6] = d[4] + a.link_base[0];
-                r[7] = d[5] + a.link_base[1];
-                r[8] = d[6] - d[8];
-                r[9] = d[7] - d[9];
-            } else {
+            if (kc < a.series_rows)
+                cur = a.series + SERIES_ROW * kc;
+            else
                 atomicOr(a.status, 4);
-            }
-            a.carry[0] = d[8];
-            a.carry[1] = d[9];
-            a.carry[2] = d[10] + a.flux_base[0];
-            a.carry[3] = d[11] + a.flux_base[1];
-            a.carry[4] = 1.0;
-            *a.step_ctr = t + 1;
         }
+        finish_rows(a, d, t, prev, cur, a.drtt_only != 0);
+        if (!a.drtt_only) *a.step_ctr = t + 1;
     }
 }
 
@@ -188,6 +212,73 @@ cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st)
     case LBM_F32: k_link_force<LBM_F32><<<grid, LINK_THREADS, 0, st>>>(a); break;
     case LBM_F32_DEV: k_link_force<LBM_F32_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
     default: k_link_force<LBM_F16_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched link force: one CTA per domain of a batch, the same sums and rows
+// as k_link_force.  The series holds rows [step][domain].  Every CTA reads the
+// shared step counter before it takes its ticket; the last CTA to arrive
+// advances the counter, so no CTA can see the new value.
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(LINK_THREADS) k_link_force_batch(BatchLinkArgs b)
+{
+    using A = typename AccOf<S>::type;
+    static_assert(sizeof(LinkArgs) % 4 == 0, "LinkArgs is copied as 32-bit words");
+    constexpr int WORDS = (int)(sizeof(LinkArgs) / 4);
+    __shared__ LinkArgs la;
+    __shared__ long long t_sh;
+    {
+        const int *src = (const int *)(b.args + blockIdx.x);
+        int *dst = (int *)&la;
+        for (int w = threadIdx.x; w < WORDS; w += LINK_THREADS) dst[w] = src[w];
+        if (threadIdx.x == 0) t_sh = *(volatile long long *)b.step_ctr;
+    }
+    __syncthreads();
+    A v[LINK_PARTIAL];
+    link_sums<S>(la, 0, b.drtt_only ? 0 : la.nlinks, 0, la.n_partials, v);
+    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(v);
+    if (threadIdx.x == 0) {
+        double d[LINK_PARTIAL];
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) d[k] = acc_double(v[k]);
+        const long long t = t_sh;
+        const long long kp = b.keep_all ? t - 1 : ((t - 1) & 1), kc = b.keep_all ? t : (t & 1);
+        const long long stride = (long long)b.n_domains * SERIES_ROW;
+        double *prev = nullptr, *cur = nullptr;
+        if (t >= 1 && la.carry[4] != 0.0) {
+            if (kp < b.series_rows)
+                prev = b.series + stride * kp + SERIES_ROW * (long long)blockIdx.x;
+            else
+                atomicOr(b.status, 4);
+        }
+        if (!b.drtt_only) {
+            if (kc < b.series_rows)
+                cur = b.series + stride * kc + SERIES_ROW * (long long)blockIdx.x;
+            else
+                atomicOr(b.status, 4);
+        }
+        finish_rows(la, d, t, prev, cur, b.drtt_only != 0);
+        __threadfence();
+        const unsigned int ticket = atomicAdd(b.ticket, 1u);
+        if (ticket == gridDim.x - 1) {
+            *b.ticket = 0u;
+            if (!b.drtt_only) *b.step_ctr = t + 1;
+        }
+    }
+}
+
+cudaError_t launch_link_force_batch(int storage, const BatchLinkArgs &b, cudaStream_t st)
+{
+    const int grid = b.n_domains;
+    if (grid < 1) return cudaSuccess;
+    switch (storage) {
+    case LBM_F64: k_link_force_batch<LBM_F64><<<grid, LINK_THREADS, 0, st>>>(b); break;
+    case LBM_F32: k_link_force_batch<LBM_F32><<<grid, LINK_THREADS, 0, st>>>(b); break;
+    case LBM_F32_DEV: k_link_force_batch<LBM_F32_DEV><<<grid, LINK_THREADS, 0, st>>>(b); break;
+    default: k_link_force_batch<LBM_F16_DEV><<<grid, LINK_THREADS, 0, st>>>(b); break;
     }
     return cudaGetLastError();
 }

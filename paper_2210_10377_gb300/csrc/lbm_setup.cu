@@ -236,7 +236,7 @@ cudaError_t launch_link_scatter(const uint16_t *nbits, int nx, int ny, int pitch
 __global__ void k_tile_flags(const uint16_t *__restrict__ nbits, int nx, int ny, int pitch,
                              int periodic, uint8_t *__restrict__ flags, int tiles_x, int rows)
 {
-    int x = blockIdx.x * TILE_X + threadIdx.x;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
     int any = 0;
     for (int r = 0; r < rows; ++r) {
         int y = blockIdx.y * rows + r;
@@ -250,11 +250,11 @@ __global__ void k_tile_flags(const uint16_t *__restrict__ nbits, int nx, int ny,
 }
 
 cudaError_t launch_tile_flags(const uint16_t *nbits, int nx, int ny, int pitch, int periodic,
-                              uint8_t *flags, int tiles_x, int tiles_y, int rows,
+                              uint8_t *flags, int tiles_x, int tiles_y, int tw, int rows,
                               cudaStream_t st)
 {
     dim3 grid(tiles_x, tiles_y);
-    k_tile_flags<<<grid, TILE_X, 0, st>>>(nbits, nx, ny, pitch, periodic, flags, tiles_x, rows);
+    k_tile_flags<<<grid, tw, 0, st>>>(nbits, nx, ny, pitch, periodic, flags, tiles_x, rows);
     return cudaGetLastError();
 }
 

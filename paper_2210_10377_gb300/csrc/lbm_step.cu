@@ -24,7 +24,7 @@ namespace gblbm {
 #define GBLBM_DIRECT_MINB_F16 8
 #endif
 #ifndef GBLBM_DIRECT_MINB_F32
-#define GBLBM_DIRECT_MINB_F32 0
+#define GBLBM_DIRECT_MINB_F32 2
 #endif
 template <int S> struct DirectMinBlocks {
     static constexpr int value = 0;

@@ -124,3 +124,67 @@ def test_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(b._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         b.lib()
+
+
+def batch_create(L, domains, **bc_fields):
+    keep = []
+    arr = (b.lbm_domain * max(len(domains), 1))()
+    for k, d in enumerate(domains):
+        m = np.ascontiguousarray(d["mask"], np.uint8)
+        u = np.ascontiguousarray(np.atleast_1d(d.get("u_in", 0.05)), np.float64)
+        keep += [m, u]
+        arr[k].mask = m.ctypes.data_as(C.POINTER(C.c_uint8))
+        arr[k].ny, arr[k].nx = m.shape
+        arr[k].tau = d.get("tau", 0.6)
+        arr[k].u_in = b._dp(u)
+        arr[k].n_u_in = u.size
+        for i in range(4):
+            arr[k].cv[i] = d.get("cv", (-1, 0, 0, 0))[i]
+    bc = b.lbm_bc()
+    L.lbm_bc_default(C.byref(bc))
+    for k, v in bc_fields.items():
+        if k == "body_force":
+            bc.body_force[0], bc.body_force[1] = v
+        else:
+            setattr(bc, k, v)
+    h = C.c_void_p()
+    rc = L.lbm_batch_create(arr, len(domains), C.byref(bc), C.byref(h))
+    return rc, L.lbm_batch_last_error(None).decode(), h
+
+
+def test_batch_rejects_bad_arguments_on_the_host(L):
+    ok = {"mask": np.zeros((8, 20), np.uint8)}
+    wall = np.zeros((8, 20), np.uint8)
+    wall[3, 1] = 1
+    cases = [
+        ([], {}, "n >= 1"),
+        ([ok, {"mask": wall}], {}, "domain 1: solid node at (1, 3)"),
+        ([ok, dict(ok, tau=0.5)], {}, "domain 1: tau"),
+        ([dict(ok, u_in=[0.05, 0.05])], {}, "domain 0: n_u_in"),
+        ([dict(ok, cv=(0, 19, 0, 7))], {}, "domain 0: control volume"),
+        ([ok], dict(body_force=(1e-6, 0.0)), "body force"),
+        ([ok], dict(kernel=1), "direct kernel"),
+        ([ok], dict(storage=9), "storage"),
+        ([ok], dict(rho0=-1.0), "rho0"),
+    ]
+    for doms, bc, needle in cases:
+        rc, msg, h = batch_create(L, doms, **bc)
+        assert rc == 1 and not h.value and needle in msg, (needle, msg)
+
+
+def test_batch_null_handle_calls_fail_cleanly(L):
+    fx, fy = C.c_double(), C.c_double()
+    assert L.lbm_batch_step(None, 1) == 1
+    assert L.lbm_batch_forces(None, 0, 0, C.byref(fx), C.byref(fy)) == 1
+    assert L.lbm_batch_steps_done(None) == -1
+    assert L.lbm_batch_nodes(None) == -1
+    assert L.lbm_batch_num_shapes() == 3
+    L.lbm_batch_destroy(None)
+
+
+def test_batch_without_device_is_an_error(L):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rc, msg, h = batch_create(L, [{"mask": np.zeros((8, 20), np.uint8)}])
+    assert rc == 3 and not h.value
