@@ -47,6 +47,9 @@ def args_():
     p.add_argument("--storage", default=None, help="f64|f32|f32dev|f16dev (profile mode)")
     p.add_argument("--kernel", default="direct", choices=["direct", "staged"],
                    help="collide-stream kernel: direct loads or staged bulk copies")
+    p.add_argument("--batch", type=int, default=0,
+                   help="profile mode: a batch of the first N domains of the 256-domain "
+                        "NACA00xx recipe instead of one workload")
     return p.parse_args()
 
 
@@ -349,7 +352,7 @@ def run_ours(a):
            "includes": "lbm_create from a pinned host mask, lbm_step(K), force series of all "
                        "four schemes read back, final populations read back, lbm_destroy"}
 
-    variants = adjoint = None
+    variants = adjoint = batch = None
     if not a.no_variants and rank == 0:
         variants = [variant(torch, binding, w, "f64", 1000, peak, local),
                     variant(torch, binding, w, "f32dev", 4000, peak, local),
@@ -358,6 +361,8 @@ def run_ours(a):
                     variant(torch, binding, inputs.PRECISION, "f32dev", 1000, peak, local)]
         adjoint = [adjoint_variant(torch, binding, inputs.DIFF, "f32", 4000, 1000, local),
                    adjoint_variant(torch, binding, w, "f32", 1000, 500, local)]
+        batch = [batch_variant(torch, binding, inputs, 256, "f32", 2000, peak, local),
+                 batch_variant(torch, binding, inputs, 256, "f16dev", 2000, peak, local)]
 
     cpu = None
     if rank == 0 and world == 1:
@@ -392,11 +397,49 @@ def run_ours(a):
             "clocks": clk,
             "variants": variants,
             "adjoint": adjoint,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def batch_domains(binding, inputs, n):
+    ws = inputs.batch_instances(256)[:n]
+    return ws, [{"mask": binding.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc),
+                 "tau": w.tau, "u_in": w.u_in} for w in ws]
+
+
+def batch_variant(torch, binding, inputs, n, storage, steps, peak, device):
+    """The batching workload: n NACA00xx domains of uneven size in one batch,
+    launch configuration from the tuner, `steps` steps timed with events."""
+    ws, doms = batch_domains(binding, inputs, n)
+    b = binding.Batch(doms, storage=storage, device=device)
+    b.step(20)
+    shape, k, tuned_ms = b.autotune(trials=5)
+    b.step(32)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flags, _ = b.status()
+    algo = BYTES_PER_UPDATE[storage] * b.nodes
+    out = {"workload": "naca00xx_batch%d_seed%d" % (n, inputs.SEED), "storage": storage, "domains": n,
+           "nodes": b.nodes, "steps": steps, "MLUPS": round(b.nodes / ms / 1e3, 1),
+           "ms_per_step": round(ms, 4),
+           "launch": {"tile": list(b.shape(shape)), "ctas_per_sm": k,
+                      "form": "persistent" if k > 0 else "one CTA per tile"},
+           "collide_stream_us": round(tuned_ms * 1e3, 1),
+           "collide_stream_GBps": round(algo / (tuned_ms / 1e3) / 1e9, 1),
+           "frac_of_measured_hbm": round(algo / (tuned_ms / 1e3) / 1e9 / peak, 4),
+           "unstable_domains": int(flags.sum())}
+    b.close()
+    return out
 
 
 def run_profile(a):
@@ -405,6 +448,22 @@ def run_profile(a):
     import torch
 
     from paper_2210_10377_gb300 import binding, inputs
+    if a.batch:
+        torch.cuda.set_device(0)
+        ws, doms = batch_domains(binding, inputs, a.batch)
+        b = binding.Batch(doms, storage=a.storage or "f32")
+        b.autotune(trials=2)
+        b.step(a.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(a.steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        print(json.dumps({"workload": "naca00xx_batch%d" % a.batch, "nodes": b.nodes,
+                          "launch": b.launch(), "steps": a.steps,
+                          "MLUPS": round(b.nodes * a.steps / el / 1e6, 1)}), flush=True)
+        b.close()
+        return 0
     w = inputs.WORKLOADS[a.workload] if a.workload else inputs.LARGE_F32
     storage = a.storage or w.storage
     torch.cuda.set_device(0)
