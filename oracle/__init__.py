@@ -14,7 +14,7 @@ import numpy as np
 
 from .build import build_oracle
 
-SCHEME_A, SCHEME_B, SCHEME_DRTT, SCHEME_A_RTT = 0, 1, 2, 3
+SCHEME_A, SCHEME_B, SCHEME_DRTT, SCHEME_A_RTT, SCHEME_SI = 0, 1, 2, 3, 4
 BC_CHANNEL, BC_PERIODIC = 0, 1
 
 _lib = None
@@ -53,6 +53,9 @@ def lib():
         L.oracle_step.restype = C.c_int
         L.oracle_force_series.argtypes = [C.c_void_p, C.c_int, C.c_long, C.c_long, dp, dp]
         L.oracle_force_series.restype = C.c_int
+        L.oracle_surface_pressure.argtypes = [C.c_void_p, C.c_double, C.c_double, ip, dp, C.c_long,
+                                              C.POINTER(C.c_long)]
+        L.oracle_surface_pressure.restype = None
         L.oracle_drtt_parts.argtypes = [C.c_void_p, C.c_long, dp]
         L.oracle_drtt_parts.restype = C.c_int
         L.oracle_adjoint.argtypes = [up, C.c_int, C.c_int, C.c_double, dp, dp, C.c_int, C.c_int,
@@ -192,6 +195,17 @@ class Sim:
     def force(self, scheme):
         fx, fy = self.force_series(scheme, self.t - 1, 1)
         return float(fx[0]), float(fy[0])
+
+    def surface_pressure(self, p_inf, q):
+        """(nodes, cp): the boundary fluid nodes (ascending node index y*nx + x) and
+        C_p = (p - p_inf)/q with p = rho/3 on the current pre-collision state."""
+        cnt = C.c_long()
+        lib().oracle_surface_pressure(self._h, float(p_inf), float(q), None, None, 0, C.byref(cnt))
+        nodes = np.zeros(max(cnt.value, 1), np.int32)
+        cp = np.zeros(max(cnt.value, 1), np.float64)
+        lib().oracle_surface_pressure(self._h, float(p_inf), float(q), _ip(nodes), _dp(cp), cnt.value,
+                                      C.byref(cnt))
+        return nodes[:cnt.value], cp[:cnt.value]
 
     def drtt_parts(self, t):
         out = np.zeros(6, np.float64)

@@ -211,7 +211,7 @@ void oracle_auto_cv(const unsigned char *mask, int nx, int ny, int periodic_x, i
 
 /* ------------------------------- the solver ------------------------------- */
 
-enum { SCHEME_A = 0, SCHEME_B = 1, SCHEME_DRTT = 2, SCHEME_A_RTT = 3, NSCHEME = 4 };
+enum { SCHEME_A = 0, SCHEME_B = 1, SCHEME_DRTT = 2, SCHEME_A_RTT = 3, SCHEME_SI = 4, NSCHEME = 5 };
 
 typedef struct oracle_sim {
     int nx, ny, periodic;
@@ -407,6 +407,40 @@ static void step_once(oracle_sim *s)
         B[1] += 2.0 * OC_Y[i] * ft[i * N + n];
     }
 
+    /* (3b) Stress integration, Eq. (stress_int), on the voxelised surface.  Each
+     *      axis link (x_f, i), i = 1..4, is a unit face between the fluid node
+     *      x_f and its solid neighbour x_f + c_i; its normal out of the solid is
+     *      n = -c_i.  The stress at x_f is T = -p I + sigma, with p = rho theta0
+     *      (theta0 = 1/3) and the deviatoric part from the second moment of the
+     *      non-equilibrium populations of the pre-collision f(x_f, t):
+     *        sigma_ab = -(1 - omega/2) sum_k (f_k - feq_k) c_ka c_kb
+     *      (the paper's factor 1 - beta with 2 beta = omega; the sign makes sigma
+     *      the viscous stress rho nu (grad u + grad u^T) of Eq. stress_int; the
+     *      theta0/D trace term sums to zero because sum_k (f_k - feq_k) = 0).
+     *      Force on the body: F_b = sum_faces n_a T_ab = -sum_faces c_ia T_ab. */
+    double SI[2] = {0.0, 0.0};
+    for (long k = 0; k < s->nlinks; ++k) {
+        long n = s->links[k] / 8;
+        int i = s->links[k] % 8 + 1;
+        if (i > 4) continue;
+        double fi[9], feq[9], rho, jx, jy;
+        for (int q = 0; q < 9; ++q) fi[q] = f[q * N + n];
+        moments(fi, &rho, &jx, &jy);
+        oracle_feq(rho, jx / rho, jy / rho, feq);
+        double Pxx = 0.0, Pxy = 0.0, Pyy = 0.0;
+        for (int q = 0; q < 9; ++q) {
+            double d = fi[q] - feq[q];
+            Pxx += d * OC_X[q] * OC_X[q];
+            Pxy += d * OC_X[q] * OC_Y[q];
+            Pyy += d * OC_Y[q] * OC_Y[q];
+        }
+        double visc = 1.0 - 0.5 * s->omega;
+        double p = rho / 3.0;
+        double Txx = -p - visc * Pxx, Txy = -visc * Pxy, Tyy = -p - visc * Pyy;
+        SI[0] -= OC_X[i] * Txx + OC_Y[i] * Txy;
+        SI[1] -= OC_X[i] * Txy + OC_Y[i] * Tyy;
+    }
+
     /* (4) Fluxes of post-collision populations through the control-volume
      *     surface (Eq. rtt7): gained = populations of fluid nodes outside the box
      *     that stream into a fluid node of the box; lost = populations of fluid
@@ -475,6 +509,8 @@ static void step_once(oracle_sim *s)
     out[SCHEME_DRTT * 2 + 1] = D[1];
     out[SCHEME_A_RTT * 2 + 0] = Ap[0];
     out[SCHEME_A_RTT * 2 + 1] = Ap[1];
+    out[SCHEME_SI * 2 + 0] = SI[0];
+    out[SCHEME_SI * 2 + 1] = SI[1];
     jout[0] = Jt[0];
     jout[1] = Jt[1];
     jout[2] = G[0];
@@ -511,6 +547,32 @@ int oracle_force_series(const oracle_sim *s, int scheme, long first, long count,
 }
 
 /* DRTT ingredients of step t: J(t) (2), gained (2), lost (2). */
+/* Pressure coefficient at the boundary fluid nodes, Section VI:
+ *   C_p = (p - p_inf) / q,  p = rho theta0 = rho / 3,
+ * on the pre-collision state of the current step.  The boundary fluid nodes
+ * are the distinct fluid nodes of the link list, ascending.  nodes and cp
+ * receive at most cap entries; *count the number of boundary nodes. */
+void oracle_surface_pressure(const oracle_sim *s, double p_inf, double q, int *nodes, double *cp,
+                             long cap, long *count)
+{
+    long m = 0;
+    long prev = -1;
+    for (long k = 0; k < s->nlinks; ++k) {
+        long n = s->links[k] / 8;
+        if (n == prev) continue;
+        prev = n;
+        if (m < cap) {
+            double fi[9], rho, jx, jy;
+            for (int i = 0; i < 9; ++i) fi[i] = s->f[i * s->N + n];
+            moments(fi, &rho, &jx, &jy);
+            if (nodes) nodes[m] = (int)n;
+            if (cp) cp[m] = (rho / 3.0 - p_inf) / q;
+        }
+        ++m;
+    }
+    *count = m;
+}
+
 int oracle_drtt_parts(const oracle_sim *s, long t, double *out6)
 {
     if (t < 0 || t >= s->t) return -1;
