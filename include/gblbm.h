@@ -84,7 +84,15 @@ typedef enum {
     /* Diagnostic, not a force: momentum the collision fails to conserve inside
      * the control volume in the storage arithmetic, sum over its fluid nodes of
      * c.(f - ft) + g; zero in exact arithmetic (BGK conserves momentum). */
-    LBM_DIAG_MOMENTUM_DEFECT = 4
+    LBM_DIAG_MOMENTUM_DEFECT = 4,
+    /* Stress integration, Eq. (stress_int), on the voxelised surface: every
+     * axis link (x_f, i), i = 1..4, is a unit face with normal -c_i out of the
+     * solid, and adds -c_i . T(x_f, t) with T = -p I + sigma from the
+     * pre-collision populations of the fluid node: p = rho theta0 (theta0 = 1/3)
+     * and sigma = -(1 - omega/2) sum_k (f_k - feq_k) c_k c_k, the viscous stress
+     * rho nu (grad u + grad u^T) (Section IV; the paper writes the factor as
+     * 1 - beta, 2 beta = omega). */
+    LBM_FORCE_SI = 5
 } lbm_scheme;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -250,6 +258,20 @@ long lbm_launch_count(const lbm_ctx *h);
 lbm_status lbm_links_noalloc(const uint8_t *d_mask, int nx, int ny, int periodic_x,
                              int32_t *d_links, long cap, long *count, void *cuda_stream);
 
+/* Pressure coefficient at the boundary fluid nodes at the current step
+ * (Section VI): cp = (p - p_inf) / q with p = rho theta0 = rho/3 from the
+ * pre-collision populations of the node.  The boundary fluid nodes are the
+ * distinct fluid nodes of the link list (a fluid node with a solid neighbour
+ * in any of the 8 directions), in ascending node index n = y*nx + x.
+ *   p_inf   reference pressure (e.g. rho0/3 of the inlet); finite.
+ *   q       dynamic pressure (e.g. rho0 u_in^2 / 2); finite, nonzero.
+ *   nodes   receives up to cap node indices (NULL: not wanted).
+ *   cp      receives up to cap coefficients, same order (NULL: not wanted).
+ *   count   receives the number of boundary fluid nodes.
+ * EINVAL for p_inf or q out of range. */
+lbm_status lbm_pressure_coefficient(lbm_ctx *h, double p_inf, double q, int32_t *nodes, double *cp, long cap,
+                                    long *count);
+
 /* Message of the last failed call on h (or of the calling thread when h is NULL). */
 const char *lbm_last_error(const lbm_ctx *h);
 
@@ -318,6 +340,11 @@ lbm_status lbm_batch_populations(lbm_batch *b, int domain, double *out);
 /* Set the pre-collision populations of one domain, before the first step
  * only (ESTATE afterwards): in is double [9][ny][nx], finite. */
 lbm_status lbm_batch_set_populations(lbm_batch *b, int domain, const double *in);
+
+/* Pressure coefficient at the boundary fluid nodes of one domain: as
+ * lbm_pressure_coefficient, node indices n = y*nx + x of that domain. */
+lbm_status lbm_batch_pressure_coefficient(lbm_batch *b, int domain, double p_inf, double q, int32_t *nodes,
+                                          double *cp, long cap, long *count);
 
 /* Per-domain instability flags: unstable[d] = 1 when domain d produced
  * rho <= 0 or NaN in some step, and first_bad_step[d] = that step (-1 when

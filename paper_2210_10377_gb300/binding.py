@@ -16,8 +16,9 @@ from . import build as _build
 CHANNEL, PERIODIC = 0, 1
 F64, F32, F32_DEV, F16_DEV = 0, 1, 2, 3
 STORAGE = {"f64": F64, "f32": F32, "f32dev": F32_DEV, "f16dev": F16_DEV}
-MEA_A, MEA_B, DRTT, MEA_A_RTT, MOMENTUM_DEFECT = 0, 1, 2, 3, 4
-SCHEMES = {"A": MEA_A, "B": MEA_B, "DRTT": DRTT, "A_RTT": MEA_A_RTT, "DEFECT": MOMENTUM_DEFECT}
+MEA_A, MEA_B, DRTT, MEA_A_RTT, MOMENTUM_DEFECT, SI = 0, 1, 2, 3, 4, 5
+SCHEMES = {"A": MEA_A, "B": MEA_B, "DRTT": DRTT, "A_RTT": MEA_A_RTT, "DEFECT": MOMENTUM_DEFECT,
+           "SI": SI}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT",
           6: "ESTATE"}
 HEADER = os.path.join(_build.ROOT, "include", "gblbm.h")
@@ -113,6 +114,11 @@ def lib():
     L.lbm_batch_launch_count.restype = C.c_longlong
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_pressure_coefficient.argtypes = [vp, C.c_double, C.c_double, C.POINTER(C.c_int32), dp, C.c_long, lp]
+    L.lbm_pressure_coefficient.restype = C.c_int
+    L.lbm_batch_pressure_coefficient.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int32), dp,
+                                                 C.c_long, lp]
+    L.lbm_batch_pressure_coefficient.restype = C.c_int
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     for name in ("lbm_batch_create", "lbm_batch_step", "lbm_batch_forces", "lbm_batch_force_series",
@@ -205,6 +211,8 @@ class Lattice:
             bc.alloc = self._alloc.alloc
             bc.free = self._alloc.free
         self.storage = bc.storage
+        self.rho0 = float(rho0)
+        self.u_ref = float(np.mean(u))
         h = C.c_void_p()
         with torch.cuda.device(device):
             _check(L.lbm_create(self.mask.ctypes.data_as(C.POINTER(C.c_uint8)), self.nx, self.ny,
@@ -282,6 +290,21 @@ class Lattice:
                                  int(checkpoint_every), C.byref(J), C.byref(dtau), _dp(du),
                                  _dp(df0) if df0 is not None else None), self._h)
         return J.value, dtau.value, du, df0
+
+    def pressure_coefficient(self, p_inf=None, q=None):
+        """(nodes, cp) at the boundary fluid nodes.  Defaults: p_inf = rho0/3 and
+        q = rho0 U^2/2, U the mean of the inlet velocity given at creation."""
+        p_inf = self.rho0 / 3.0 if p_inf is None else p_inf
+        q = 0.5 * self.rho0 * self.u_ref ** 2 if q is None else q
+        cnt = C.c_long()
+        _check(lib().lbm_pressure_coefficient(self._h, float(p_inf), float(q), None, None, 0, C.byref(cnt)),
+               self._h)
+        nodes = np.zeros(max(cnt.value, 1), np.int32)
+        cp = np.zeros(max(cnt.value, 1))
+        _check(lib().lbm_pressure_coefficient(self._h, float(p_inf), float(q),
+                                              nodes.ctypes.data_as(C.POINTER(C.c_int32)), _dp(cp), cnt.value,
+                                              C.byref(cnt)), self._h)
+        return nodes[:cnt.value], cp[:cnt.value]
 
     @property
     def steps_done(self):
@@ -399,6 +422,18 @@ class Batch:
     def set_populations(self, domain, f):
         f = np.ascontiguousarray(f, np.float64)
         _bcheck(lib().lbm_batch_set_populations(self._h, int(domain), _dp(f)), self._h)
+
+    def pressure_coefficient(self, domain, p_inf, q):
+        """(nodes, cp) at the boundary fluid nodes of one domain."""
+        cnt = C.c_long()
+        _bcheck(lib().lbm_batch_pressure_coefficient(self._h, int(domain), float(p_inf), float(q), None, None, 0,
+                                                     C.byref(cnt)), self._h)
+        nodes = np.zeros(max(cnt.value, 1), np.int32)
+        cp = np.zeros(max(cnt.value, 1))
+        _bcheck(lib().lbm_batch_pressure_coefficient(self._h, int(domain), float(p_inf), float(q),
+                                                     nodes.ctypes.data_as(C.POINTER(C.c_int32)), _dp(cp),
+                                                     cnt.value, C.byref(cnt)), self._h)
+        return nodes[:cnt.value], cp[:cnt.value]
 
     def status(self):
         n = self.num_domains

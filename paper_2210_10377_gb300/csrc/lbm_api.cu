@@ -60,6 +60,8 @@ struct lbm_ctx {
     uint8_t *tile_flag = nullptr;
     int32_t *links = nullptr;
     long long nlinks = 0;
+    int32_t *bnodes = nullptr;  // boundary fluid nodes (distinct link nodes, ascending)
+    long long n_bnodes = 0;
     double *u_row = nullptr;
     void *inlet = nullptr;
     double *partials = nullptr;  // NBUF slices, one per destination buffer
@@ -238,6 +240,8 @@ LinkArgs link_args(lbm_ctx *h, int src, int dst, int precollision, int drtt_only
     a.record_series = h->record_series;
     a.drtt_only = drtt_only;
     a.rho0 = h->rho0;
+    a.visc = 1.0 - 0.5 * h->omega;
+    a.visc_f = (float)a.visc;
     memcpy(a.link_base, h->link_base, sizeof(a.link_base));
     memcpy(a.flux_base, h->flux_base, sizeof(a.flux_base));
     return a;
@@ -390,6 +394,7 @@ void free_all(lbm_ctx *h)
         if (e) cudaEventDestroy(e);
     if (h->side) cudaStreamDestroy(h->side);
     void *bufs[] = {h->pop_base[0], h->pop_base[1], h->pop_base[2], h->mask_d, h->nbits, h->tile_flag, h->links,
+                    h->bnodes,
                     h->u_row, h->inlet, h->partials, h->link_partials, h->ticket, h->series,
                     h->carry, h->step_ctr, h->status};
     for (void *p : bufs) dev_free(h, p);
@@ -604,11 +609,21 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     dev_free(h, blk);
     dev_free(h, total_d);
     if (le != cudaSuccess) return fail(cuda_err(h, le, "link list"));
+    {
+        ALLOC(h->bnodes, int32_t *, sizeof(int32_t) * (h->nlinks > 0 ? h->nlinks : 1));
+        long long *cnt_d = (long long *)dev_alloc(h, sizeof(long long));
+        if (!cnt_d) return fail(set_err(h, LBM_ENOMEM, "device allocation failed"));
+        cudaError_t be = launch_boundary_nodes(h->links, h->nlinks, h->bnodes, cnt_d, s);
+        if (be == cudaSuccess) be = cudaMemcpyAsync(&h->n_bnodes, cnt_d, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (be == cudaSuccess) be = cudaStreamSynchronize(s);
+        dev_free(h, cnt_d);
+        if (be != cudaSuccess) return fail(cuda_err(h, be, "boundary nodes"));
+    }
     CKC(launch_init(h->storage, h->pop[0], h->plane, h->mask_d, nx, ny, h->pitch, h->u_row, h->rho0,
                     h->inlet, s),
         "initial state");
     CKC(cudaStreamSynchronize(s), "sync");
-    h->launches = 6;
+    h->launches = 7;
 #undef CKC
 #undef ALLOC
     *out = h;
@@ -680,7 +695,7 @@ lbm_status lbm_step(lbm_ctx *h, int n)
 lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, double *fx, double *fy)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
-    if (scheme < 0 || scheme > 4) return set_err(h, LBM_EINVAL, "unknown scheme %d", scheme);
+    if (scheme < 0 || scheme > LBM_FORCE_SI) return set_err(h, LBM_EINVAL, "unknown scheme %d", scheme);
     if (count < 0 || first < 0 || first + count > h->t)
         return set_err(h, LBM_EINVAL, "steps [%ld, %ld) outside [0, %lld)", first, first + count, h->t);
     if (count == 0) return LBM_OK;
@@ -704,7 +719,7 @@ lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, doub
                "D2H series");
     }
     CK(h, cudaStreamSynchronize(h->stream), "sync");
-    const int col = 2 * scheme;  // row: A, B, DRTT, A', defect (x, y each)
+    const int col = 2 * scheme;  // row: A, B, DRTT, A', defect, SI (x, y each)
     for (long k = 0; k < count; ++k) {
         fx[k] = rows[R * k + col];
         fy[k] = rows[R * k + col + 1];
@@ -773,6 +788,33 @@ lbm_status lbm_set_populations(lbm_ctx *h, const double *in)
     h->precollision = 1;
     h->carry_from = h->t;
     if (h->drtt_ready < h->t) h->drtt_ready = h->t;
+    return LBM_OK;
+}
+
+lbm_status lbm_pressure_coefficient(lbm_ctx *h, double p_inf, double q, int32_t *nodes, double *cp, long cap,
+                                    long *count)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (!std::isfinite(p_inf) || !std::isfinite(q) || q == 0.0)
+        return set_err(h, LBM_EINVAL, "p_inf must be finite and q finite and nonzero");
+    if (count) *count = (long)h->n_bnodes;
+    const long n = cap < (long)h->n_bnodes ? cap : (long)h->n_bnodes;
+    if (n <= 0) return LBM_OK;
+    if (nodes)
+        CK(h, cudaMemcpyAsync(nodes, h->bnodes, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream), "D2H nodes");
+    if (cp) {
+        double *d = (double *)dev_alloc(h, sizeof(double) * h->n_bnodes);
+        if (!d) return set_err(h, LBM_ENOMEM, "scratch allocation failed");
+        cudaError_t e = launch_surface_pressure(h->storage, h->pop[h->cur], h->nbits, h->bnodes, h->n_bnodes, h->plane,
+                                                h->nx, h->ny, h->pitch, h->periodic, h->precollision, h->rho0, p_inf,
+                                                q, d, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cp, d, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        dev_free(h, d);
+        h->launches += 1;
+        if (e != cudaSuccess) return cuda_err(h, e, "surface pressure");
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "sync");
     return LBM_OK;
 }
 

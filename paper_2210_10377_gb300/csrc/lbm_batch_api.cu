@@ -38,6 +38,7 @@ struct Domain {
     long long row_off = 0;    // entries into the u_row arena (ny)
     long long inlet_off = 0;  // elements into the inlet arena (9*ny)
     long long link_off = 0, nlinks = 0;
+    long long n_bnodes = 0;   // boundary fluid nodes (at link_off in the boundary-node arena)
     double link_base[2] = {0, 0}, flux_base[2] = {0, 0};
     int cvt[BATCH_SHAPES][4];
     int n_cv_tiles[BATCH_SHAPES];
@@ -69,6 +70,7 @@ struct lbm_batch {
     double *u_row = nullptr;
     void *inlet = nullptr;
     int32_t *links = nullptr;
+    int32_t *bnodes = nullptr;        // boundary fluid nodes of every domain, at its link offset
     double *partials = nullptr;       // [max over shapes of the partial rows][CV_PARTIAL]
     double *tune_partials = nullptr;  // the tuner's scratch copy of it
     uint8_t *checked[BATCH_SHAPES] = {nullptr, nullptr, nullptr};     // per tile, batch order
@@ -159,7 +161,7 @@ void free_all(lbm_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     void *bufs[] = {b->pop_base[0], b->pop_base[1], b->mask_d, b->nbits, b->u_row, b->inlet,
-                    b->links, b->partials, b->tune_partials, b->checked[0], b->checked[1],
+                    b->links, b->bnodes, b->partials, b->tune_partials, b->checked[0], b->checked[1],
                     b->checked[2], b->checked_cv[0], b->checked_cv[1], b->checked_cv[2], b->largs,
                     b->series, b->carry, b->step_ctr, b->ticket, b->status, b->tune_status,
                     b->bstatus};
@@ -243,6 +245,8 @@ LinkArgs link_args(const lbm_batch *b, int d, int s, int src)
     a.precollision = src < 0 ? 1 : 0;
     a.record_series = b->record_series;
     a.rho0 = b->rho0;
+    a.visc = 1.0 - 0.5 / m.tau;
+    a.visc_f = (float)a.visc;
     memcpy(a.link_base, m.link_base, sizeof(a.link_base));
     memcpy(a.flux_base, m.flux_base, sizeof(a.flux_base));
     return a;
@@ -603,9 +607,21 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
         b->launches += 1;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_scratch(bcuda(b, e, "link lists"));
+    b->bnodes = (int32_t *)bdev_alloc(b, sizeof(int32_t) * (links_total > 0 ? links_total : 1));
+    if (!b->bnodes) return fail_scratch(berr(b, LBM_ENOMEM, "device allocation of boundary nodes failed"));
+    for (int d = 0; d < n && e == cudaSuccess; ++d) {
+        const Domain &m = b->dom[d];
+        e = launch_boundary_nodes(b->links + m.link_off, m.nlinks, b->bnodes + m.link_off, totals_d + d, s);
+        b->launches += 1;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(totals.data(), totals_d, sizeof(long long) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     bdev_free(b, blk);
     bdev_free(b, totals_d);
-    if (e != cudaSuccess) return fail(bcuda(b, e, "link lists"));
+    if (e != cudaSuccess) return fail(bcuda(b, e, "boundary nodes"));
+    for (int d = 0; d < n; ++d) b->dom[d].n_bnodes = totals[d];
 
     // tile flags and tables, every shape
     for (int sh = 0; sh < BATCH_SHAPES; ++sh) {
@@ -746,7 +762,7 @@ lbm_status read_rows(lbm_batch *b, int domain, long first, long count, std::vect
 
 lbm_status check_range(lbm_batch *b, int scheme, long first, long count)
 {
-    if (scheme < 0 || scheme > 4) return berr(b, LBM_EINVAL, "unknown scheme %d", scheme);
+    if (scheme < 0 || scheme > LBM_FORCE_SI) return berr(b, LBM_EINVAL, "unknown scheme %d", scheme);
     if (count < 0 || first < 0 || first + count > b->t)
         return berr(b, LBM_EINVAL, "steps [%ld, %ld) outside [0, %lld)", first, first + count, b->t);
     if (!b->record_series && first < b->t - 2)
@@ -841,6 +857,35 @@ lbm_status lbm_batch_set_populations(lbm_batch *b, int domain, const double *in)
     }
     bdev_free(b, scratch);
     return st;
+}
+
+lbm_status lbm_batch_pressure_coefficient(lbm_batch *b, int domain, double p_inf, double q, int32_t *nodes,
+                                          double *cp, long cap, long *count)
+{
+    if (!b) return berr(nullptr, LBM_EINVAL, "NULL handle");
+    if (domain < 0 || domain >= b->n) return berr(b, LBM_EINVAL, "no domain %d", domain);
+    if (!std::isfinite(p_inf) || !std::isfinite(q) || q == 0.0)
+        return berr(b, LBM_EINVAL, "p_inf must be finite and q finite and nonzero");
+    const Domain &m = b->dom[domain];
+    if (count) *count = (long)m.n_bnodes;
+    const long n = cap < (long)m.n_bnodes ? cap : (long)m.n_bnodes;
+    if (n <= 0) return LBM_OK;
+    const int32_t *bn = b->bnodes + m.link_off;
+    if (nodes) BCK(b, cudaMemcpyAsync(nodes, bn, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream), "D2H nodes");
+    if (cp) {
+        double *d = (double *)bdev_alloc(b, sizeof(double) * m.n_bnodes);
+        if (!d) return berr(b, LBM_ENOMEM, "scratch allocation failed");
+        cudaError_t e = launch_surface_pressure(b->storage, b->pop[b->cur] + m.pop_off * (long long)b->elem,
+                                                b->nbits + m.node_off, bn, m.n_bnodes, m.plane, m.nx, m.ny, m.pitch,
+                                                b->periodic, b->t == 0 ? 1 : 0, b->rho0, p_inf, q, d, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cp, d, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        bdev_free(b, d);
+        b->launches += 1;
+        if (e != cudaSuccess) return bcuda(b, e, "surface pressure");
+    }
+    BCK(b, cudaStreamSynchronize(b->stream), "sync");
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_status(lbm_batch *b, int *unstable, long *first_bad_step)

@@ -16,7 +16,7 @@
 //                post-collision state, and gained-minus-lost(t); FP64 for FP64
 //                storage, float-float pairs otherwise (8 bytes either way);
 //   link_partials [n_ctas][12] per-CTA rows of the link kernel, same types;
-//   series       double [steps][10]: A, B, DRTT, A', momentum defect (x, y);
+//   series       double [steps][12]: A, B, DRTT, A', momentum defect, SI (x, y each);
 //   carry        double [8]: J_post(t-1), GL(t-1), flag;  step counter int64;
 //   ticket       uint32 arrival counter of the link kernel's CTAs.
 #pragma once
@@ -37,8 +37,8 @@ constexpr int PITCH_ALIGN = 64;
 constexpr int LINK_THREADS = 128;
 constexpr int MAX_LINK_CTAS = 148;
 constexpr int CV_PARTIAL = 6;
-constexpr int LINK_PARTIAL = 12;
-constexpr int SERIES_ROW = 10;
+constexpr int LINK_PARTIAL = 14;
+constexpr int SERIES_ROW = 12;
 
 __host__ __device__ constexpr int tile_rows(int storage)
 {
@@ -141,6 +141,8 @@ struct LinkArgs {
     int record_series;
     int drtt_only;           // finalise DRTT(T-1) from a momentum-only pass
     double rho0;
+    double visc;             // 1 - omega/2: deviatoric stress = -visc * non-equilibrium second moment
+    float visc_f;
     double link_base[2];     // deviation storage: 2 rho0 sum_links c_i w_i
     double flux_base[2];     // deviation storage: rho0 (sum_in - sum_out) c_i w_i
 };
@@ -178,6 +180,12 @@ cudaError_t launch_gather(int storage, const void *pop, const uint16_t *nbits, c
                           long long plane, int nx, int ny, int pitch, int periodic,
                           int precollision, double rho0, int plane_i, double *out,
                           cudaStream_t st);
+cudaError_t launch_boundary_nodes(const int32_t *links, long long nlinks, int32_t *nodes, long long *count,
+                                  cudaStream_t st);
+cudaError_t launch_surface_pressure(int storage, const void *pop, const uint16_t *nbits, const int32_t *nodes,
+                                    long long count, long long plane, int nx, int ny, int pitch, int periodic,
+                                    int precollision, double rho0, double p_inf, double q, double *cp,
+                                    cudaStream_t st);
 cudaError_t launch_scatter_pop(int storage, void *pop, const uint16_t *nbits, long long plane,
                                int nx, int ny, int pitch, double rho0, int plane_i,
                                const double *in, cudaStream_t st);

@@ -7,6 +7,8 @@
 // k_link_force_batch: the same for every domain of a batch, one CTA each.
 // k_gather / k_scatter: one population plane between the device storage and
 //   an FP64 [ny][nx] array (pre-collision f(x, T) reconstructed by a pull).
+// k_boundary_nodes / k_surface_pressure: the boundary fluid nodes and their
+//   pressure coefficient (Section VI).
 //
 // Reductions are deterministic (fixed trees, no floating-point atomics).
 #include "lbm_batch.cuh"
@@ -16,8 +18,18 @@ namespace gblbm {
 
 // ---------------------------------------------------------------------------
 // Per-link momentum exchange of step t over links [k0, k1) and the sum of the
-// control-volume partial rows [p0, p1) (Eqs. MEA, rtt4, rtt5, rtt7):
-// v: A(2), B(2), A'(2), J_pre(2), J_post(2), GL(2).
+// control-volume partial rows [p0, p1) (Eqs. MEA, rtt4, rtt5, rtt7), and the
+// stress integral (Eq. stress_int) over the axis links:
+// v: A(2), B(2), A'(2), J_pre(2), J_post(2), GL(2), SI(2).
+//
+// Stress integration: an axis link (x_f, i), i = 1..4, is a unit face of the
+// voxelised surface with normal -c_i out of the solid; it adds -c_i.T(x_f)
+// with T = -p I + sigma on the pre-collision f(x_f, t): p = rho/3 and sigma =
+// -(1 - omega/2) (sum_k f_k c_k c_k - rho/3 I - rho u u), the non-equilibrium
+// second moment written with the equilibrium's closed-form moments.  The
+// pressure enters as (rho - rho0)/3: the faces of any solid come in opposite
+// pairs along each axis, so the constant rho0/3 sums to zero, and leaving it
+// out keeps the FP32 sums free of its cancellation.
 // ---------------------------------------------------------------------------
 template <int S>
 __device__ __forceinline__ void link_sums(const LinkArgs &a, long long k0, long long k1, int p0, int p1,
@@ -66,6 +78,49 @@ __device__ __forceinline__ void link_sums(const LinkArgs &a, long long k0, long 
             sb = {2.0f * ft, 0.0f};
             sp = ff_two_sum(fi, ft);
         }
+        if (i <= 4) {
+            constexpr bool DEV = Traits<S>::dev;
+            T g[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                if (a.precollision) {
+                    g[q] = to_comp(src[q * plane + idx]);
+                } else if (a.nbits[idx] & (1u << opp(q))) {
+                    g[q] = to_comp(src[opp(q) * plane + idx]);
+                } else {
+                    int sx = x - cx(q), sy = y - cy(q);
+                    if (a.periodic) sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+                    sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+                    g[q] = to_comp(src[q * plane + (long long)sy * a.pitch + sx]);
+                }
+            }
+            const T r0 = (T)a.rho0;
+            const T jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
+            const T jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
+            const T sum = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
+            // deviation storage holds f - w rho0: sum = rho - rho0, and the base
+            // adds rho0/3 to the diagonal second moments
+            const T drho = DEV ? sum : sum - r0;
+            const T rho = r0 + drho;
+            const T inv = T(1) / rho;
+            const T ux = jx * inv, uy = jy * inv;
+            const T diag = ((g[5] + g[6]) + (g[7] + g[8]));
+            const T mxx = (g[1] + g[3]) + diag, myy = (g[2] + g[4]) + diag;
+            const T mxy = (g[5] - g[6]) + (g[7] - g[8]);
+            // sum f c c - rho/3 I - rho u u, with sum f c_x^2 = mxx (+ rho0/3 for deviations)
+            const T third = T(1) / T(3);
+            const T pxx = DEV ? (mxx - drho * third) - rho * ux * ux : (mxx - rho * third) - rho * ux * ux;
+            const T pyy = DEV ? (myy - drho * third) - rho * uy * uy : (myy - rho * third) - rho * uy * uy;
+            const T pxy = mxy - rho * ux * uy;
+            const T visc = sizeof(T) == 8 ? (T)a.visc : (T)a.visc_f;
+            const T pp = drho * third;
+            const T txx = -pp - visc * pxx, tyy = -pp - visc * pyy, txy = -visc * pxy;
+            // -c_i . T on the face
+            const T fsx = cx(i) != 0 ? (cx(i) > 0 ? -txx : txx) : (cy(i) > 0 ? -txy : txy);
+            const T fsy = cx(i) != 0 ? (cx(i) > 0 ? -txy : txy) : (cy(i) > 0 ? -tyy : tyy);
+            acc_add(v[12], as_acc(fsx, A()));
+            acc_add(v[13], as_acc(fsy, A()));
+        }
         const int ex = cx(i), ey = cy(i);
         if (ex != 0) {
             acc_add(v[0], ex > 0 ? sa : -sa);
@@ -109,6 +164,8 @@ __device__ __forceinline__ void finish_rows(const LinkArgs &a, const double (&d)
         cur[7] = d[5] + a.link_base[1];
         cur[8] = d[6] - d[8];
         cur[9] = d[7] - d[9];
+        cur[10] = d[12];
+        cur[11] = d[13];
     }
     a.carry[0] = d[8];
     a.carry[1] = d[9];
@@ -124,7 +181,7 @@ __device__ __forceinline__ void finish_rows(const LinkArgs &a, const double (&d)
 // ticket) sums the rows in slot order, so the result does not depend on which
 // CTA finishes last, and completes the step's series row and the DRTT of the
 // previous step.
-// Series row t: A(2) B(2) DRTT(2) A'(2) defect(2), where defect is the
+// Series row t: A(2) B(2) DRTT(2) A'(2) defect(2) SI(2), where defect is the
 // collision's momentum defect inside the box, J_pre(t) - J_post(t).
 // For deviation storage the momentum of the base w_i rho0 over the links and
 // over the box-surface crossings is a fixed geometric sum (link_base,
@@ -288,23 +345,17 @@ cudaError_t launch_link_force_batch(int storage, const BatchLinkArgs &b, cudaStr
 // After a step the buffer holds ft(T-1); f(T) is its pull with bounce-back,
 // the inlet column's stored feq and the outlet copy of column nx-2.
 // ---------------------------------------------------------------------------
+// f_i(x, y, T) (FP64, the full population for deviation storage) of a fluid node.
 template <int S>
-__global__ void k_gather(const typename Traits<S>::store_t *__restrict__ pop,
-                         const uint16_t *__restrict__ nbits, long long plane, int nx, int ny,
-                         int pitch, int periodic, int precollision, double rho0, int i,
-                         double *__restrict__ out)
+__device__ __forceinline__ double pulled_value(const typename Traits<S>::store_t *__restrict__ pop,
+                                               const uint16_t *__restrict__ nbits, long long plane, int nx,
+                                               int ny, int pitch, int periodic, int precollision, double rho0,
+                                               int x, int y, int i)
 {
     constexpr bool DEV = Traits<S>::dev;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= nx) return;
     const long long idx = (long long)y * pitch + x;
-    double v;
-    if (nbits[idx] & 1) {
-        out[(long long)y * nx + x] = 0.0;
-        return;
-    }
     const bool channel = !periodic;
+    double v;
     if (precollision || (channel && x == 0)) {
         v = (double)to_comp(pop[i * plane + idx]);
     } else {
@@ -321,7 +372,115 @@ __global__ void k_gather(const typename Traits<S>::store_t *__restrict__ pop,
         }
     }
     if (DEV) v += wgt<double>(i) * rho0;
-    out[(long long)y * nx + x] = v;
+    return v;
+}
+
+template <int S>
+__global__ void k_gather(const typename Traits<S>::store_t *__restrict__ pop,
+                         const uint16_t *__restrict__ nbits, long long plane, int nx, int ny,
+                         int pitch, int periodic, int precollision, double rho0, int i,
+                         double *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= nx) return;
+    const long long idx = (long long)y * pitch + x;
+    out[(long long)y * nx + x] =
+        (nbits[idx] & 1) ? 0.0 : pulled_value<S>(pop, nbits, plane, nx, ny, pitch, periodic, precollision, rho0, x, y, i);
+}
+
+// ---------------------------------------------------------------------------
+// Boundary fluid nodes: the distinct nodes of the ascending link list, by one
+// CTA walking the list in chunks with a block-wide prefix count.
+// ---------------------------------------------------------------------------
+constexpr int BNODE_THREADS = 1024;
+
+__global__ void __launch_bounds__(BNODE_THREADS)
+    k_boundary_nodes(const int32_t *__restrict__ links, long long nlinks, int32_t *__restrict__ nodes,
+                     long long *__restrict__ count)
+{
+    __shared__ int warp_sum[BNODE_THREADS / 32];
+    __shared__ long long base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (long long k0 = 0; k0 < nlinks; k0 += BNODE_THREADS) {
+        const long long k = k0 + threadIdx.x;
+        int first = 0, node = 0;
+        if (k < nlinks) {
+            node = links[k] >> 3;
+            first = (k == 0 || (links[k - 1] >> 3) != node) ? 1 : 0;
+        }
+        int incl = first;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = warp_sum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += v;
+            }
+            warp_sum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const int before = (warp > 0 ? warp_sum[warp - 1] : 0) + incl - first;
+        if (first) nodes[base + before] = node;
+        __syncthreads();
+        if (threadIdx.x == BNODE_THREADS - 1) base += before + first;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+cudaError_t launch_boundary_nodes(const int32_t *links, long long nlinks, int32_t *nodes, long long *count,
+                                  cudaStream_t st)
+{
+    k_boundary_nodes<<<1, BNODE_THREADS, 0, st>>>(links, nlinks, nodes, count);
+    return cudaGetLastError();
+}
+
+// Pressure coefficient at boundary fluid nodes (Section VI):
+// cp = (rho/3 - p_inf) / q with rho from the pre-collision populations.
+template <int S>
+__global__ void k_surface_pressure(const typename Traits<S>::store_t *__restrict__ pop,
+                                   const uint16_t *__restrict__ nbits, const int32_t *__restrict__ nodes,
+                                   long long count, long long plane, int nx, int ny, int pitch, int periodic,
+                                   int precollision, double rho0, double p_inf, double q, double *__restrict__ cp)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int n = nodes[k];
+    const int x = n % nx, y = n / nx;
+    double rho = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rho += pulled_value<S>(pop, nbits, plane, nx, ny, pitch, periodic, precollision, rho0, x, y, i);
+    cp[k] = (rho / 3.0 - p_inf) / q;
+}
+
+cudaError_t launch_surface_pressure(int storage, const void *pop, const uint16_t *nbits, const int32_t *nodes,
+                                    long long count, long long plane, int nx, int ny, int pitch, int periodic,
+                                    int precollision, double rho0, double p_inf, double q, double *cp,
+                                    cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const int blocks = (int)((count + 127) / 128);
+#define GBLBM_SP(S, T)                                                                                   \
+    k_surface_pressure<S><<<blocks, 128, 0, st>>>((const T *)pop, nbits, nodes, count, plane, nx, ny, pitch, \
+                                                  periodic, precollision, rho0, p_inf, q, cp)
+    switch (storage) {
+    case LBM_F64: GBLBM_SP(LBM_F64, double); break;
+    case LBM_F32: GBLBM_SP(LBM_F32, float); break;
+    case LBM_F32_DEV: GBLBM_SP(LBM_F32_DEV, float); break;
+    default: GBLBM_SP(LBM_F16_DEV, __half); break;
+    }
+#undef GBLBM_SP
+    return cudaGetLastError();
 }
 
 template <int S>

@@ -17,9 +17,9 @@ from paper_2210_10377_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-SCHEMES = ("A", "B", "DRTT", "A_RTT")
+SCHEMES = ("A", "B", "DRTT", "A_RTT", "SI")
 ORACLE_SCHEME = {"A": oracle.SCHEME_A, "B": oracle.SCHEME_B, "DRTT": oracle.SCHEME_DRTT,
-                 "A_RTT": oracle.SCHEME_A_RTT}
+                 "A_RTT": oracle.SCHEME_A_RTT, "SI": oracle.SCHEME_SI}
 
 
 @pytest.fixture(scope="module")
@@ -116,6 +116,10 @@ def test_batch_equals_single_domain_handles(gb, storage):
         lat = gb.Lattice(d["mask"], d["tau"], d["u_in"], storage=storage)
         lat.step(steps)
         assert np.array_equal(b.populations(k), lat.populations()), k
+        q = 0.5 * 0.05 ** 2
+        bn, bc = b.pressure_coefficient(k, 1.0 / 3.0, q)
+        ln, lc = lat.pressure_coefficient(1.0 / 3.0, q)
+        assert np.array_equal(bn, ln) and np.array_equal(bc, lc), k
         ser = {s: lat.force_series(s) for s in SCHEMES}
         sc = scale_of(ser)
         for s in SCHEMES:
@@ -153,7 +157,7 @@ def test_batch_launch_configs_agree(gb):
             continue
         for d in range(len(doms)):
             assert np.array_equal(got[0][d], ref[0][d]), (shape, k, d)
-            for s in ("A", "B", "A_RTT"):
+            for s in ("A", "B", "A_RTT", "SI"):
                 assert np.array_equal(got[1][(d, s)][0], ref[1][(d, s)][0]), (shape, k, d, s)
             sc = np.abs(ref[1][(d, "B")][0]).max()
             assert np.abs(got[1][(d, "DRTT")][0] - ref[1][(d, "DRTT")][0]).max() <= 1e-12 * sc
@@ -175,7 +179,7 @@ def test_batch_autotune_leaves_the_state_alone_and_splits_agree(gb):
     assert a.steps_done == b.steps_done == 2600
     for d in range(len(doms)):
         assert np.array_equal(a.populations(d), b.populations(d)), d
-        for s in ("A", "B", "A_RTT"):
+        for s in ("A", "B", "A_RTT", "SI"):
             assert np.array_equal(a.force_series(d, s)[0], b.force_series(d, s)[0]), (d, s)
             assert np.array_equal(a.force_series(d, s)[1], b.force_series(d, s)[1]), (d, s)
     a.close()
@@ -215,7 +219,7 @@ def test_batch_checkpoint_resume_bitwise(gb):
     c.step(40)
     for d in range(3):
         assert np.array_equal(a.populations(d), c.populations(d))
-        for s in ("A", "B", "A_RTT"):
+        for s in ("A", "B", "A_RTT", "SI"):
             assert np.array_equal(a.force_series(d, s, 41, 39)[0], c.force_series(d, s, 1, 39)[0])
     with pytest.raises(gb.LbmError) as e:
         c.set_populations(0, states[0])

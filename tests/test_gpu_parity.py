@@ -14,9 +14,9 @@ from paper_2210_10377_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-SCHEMES = ("A", "B", "DRTT", "A_RTT")
+SCHEMES = ("A", "B", "DRTT", "A_RTT", "SI")
 ORACLE_SCHEME = {"A": oracle.SCHEME_A, "B": oracle.SCHEME_B, "DRTT": oracle.SCHEME_DRTT,
-                 "A_RTT": oracle.SCHEME_A_RTT}
+                 "A_RTT": oracle.SCHEME_A_RTT, "SI": oracle.SCHEME_SI}
 
 
 @pytest.fixture(scope="module")
@@ -159,7 +159,7 @@ def test_reduced_precision_forces_small_naca(gb, storage, tol):
     m = naca(w, 4.0)
     sim, lat = run_pair(gb, m, w.tau, w.u_in, 600, storage=storage)
     scale = force_scale(sim)
-    for s in ("A", "B", "A_RTT"):
+    for s in ("A", "B", "A_RTT", "SI"):
         ox, oy = sim.force_series(ORACLE_SCHEME[s])
         gx, gy = lat.force_series(s)
         assert np.abs(gx - ox).max() <= tol * max(scale, np.abs(ox).max()), s
@@ -355,7 +355,7 @@ def test_staged_kernel_matches_direct_kernel(gb, storage):
             runs.append(lat)
         a, b = runs
         assert np.array_equal(a.populations(), b.populations())
-        for s in ("A", "B", "A_RTT"):
+        for s in ("A", "B", "A_RTT", "SI"):
             assert np.array_equal(a.force_series(s)[0], b.force_series(s)[0]), s
             assert np.array_equal(a.force_series(s)[1], b.force_series(s)[1]), s
         scale = np.abs(a.force_series("B")[0]).max()
@@ -411,9 +411,36 @@ def test_force_series_2000_steps_scaled_bench_geometry(gb, storage, tol):
     m = naca(w)
     sim, lat = run_pair(gb, m, w.tau, w.u_in, 2000, storage=storage, chunks=[7, 1993])
     scale = force_scale(sim)
-    for s in ("B", "DRTT", "A", "A_RTT"):
+    for s in ("B", "DRTT", "A", "A_RTT", "SI"):
         ox, oy = sim.force_series(ORACLE_SCHEME[s])
         gx, gy = lat.force_series(s)
         sc = max(scale, np.abs(ox).max()) if s in ("A", "A_RTT") else scale
         assert np.abs(gx - ox).max() <= tol * sc, s
         assert np.abs(gy - oy).max() <= tol * sc, s
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev"])
+def test_pressure_coefficient_matches_oracle(gb, storage):
+    # C_p at the boundary fluid nodes (Section VI), at the pre-collision start
+    # state and after 1 and 300 steps.  The kernel is checked against the
+    # oracle's C_p of the GPU's own state (read back, 1e-12); in FP64 also
+    # against the oracle's trajectory.  (A reduced-precision trajectory's mean
+    # density drifts by ~1e-6 from FP64, which moves every C_p by drho/(3q).)
+    w = inputs.SMALL_F64
+    m = naca(w, 4.0)
+    q, p_inf = 0.5 * w.u_in ** 2, 1.0 / 3.0
+    sim = oracle.Sim(m, w.tau, w.u_in)
+    lat = gb.Lattice(m, w.tau, w.u_in, storage=storage)
+    for n in (0, 1, 299):
+        sim.step(n)
+        lat.step(n)
+        gn, gc = lat.pressure_coefficient(p_inf, q)
+        here = oracle.Sim(m, w.tau, w.u_in)
+        here.set_populations(lat.populations())
+        hn, hc = here.surface_pressure(p_inf, q)
+        assert hn.size > 0 and np.array_equal(hn, gn)
+        assert np.abs(gc - hc).max() <= 1e-12, n
+        if storage == "f64":
+            on, oc = sim.surface_pressure(p_inf, q)
+            assert np.array_equal(on, gn) and np.abs(gc - oc).max() <= 1e-10, n
+    lat.close()
