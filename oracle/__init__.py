@@ -32,6 +32,8 @@ def lib():
         L.oracle_naca_mask.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_int, up]
         L.oracle_naca_mask.restype = C.c_int
+        L.oracle_cylinder_mask.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, up]
+        L.oracle_cylinder_mask.restype = C.c_int
         L.oracle_naca_thickness.argtypes = [C.c_double, C.c_double, C.c_int]
         L.oracle_naca_thickness.restype = C.c_double
         L.oracle_links.argtypes = [up, C.c_int, C.c_int, C.c_int, ip, C.c_long]
@@ -90,6 +92,16 @@ def lattice():
 def feq(rho, ux, uy):
     out = np.zeros(9, np.float64)
     lib().oracle_feq(float(rho), float(ux), float(uy), _dp(out))
+    return out
+
+
+def cylinder_mask(nx, ny, xc, yc, diameter):
+    """uint8 [ny][nx], 1 where (x - xc)^2 + (y - yc)^2 <= (diameter/2)^2."""
+    out = np.zeros((ny, nx), np.uint8)
+    rc = lib().oracle_cylinder_mask(int(nx), int(ny), float(xc), float(yc), 0.5 * float(diameter),
+                                    out.ctypes.data_as(C.POINTER(C.c_ubyte)))
+    if rc != 0:
+        raise ValueError("bad cylinder arguments")
     return out
 
 

@@ -129,6 +129,23 @@ int oracle_naca_mask(int nx, int ny, double chord, double thickness, double alph
     return 0;
 }
 
+/* ---- Circular cylinder (Section VI, flow past a 2-D circular cylinder):
+ * node (x, y) is solid iff (x - xc)^2 + (y - yc)^2 <= r^2, r = D/2, evaluated
+ * as written (dx*dx + dy*dy compared with r*r) in double precision with no
+ * fused multiply-add. */
+int oracle_cylinder_mask(int nx, int ny, double xc, double yc, double radius, unsigned char *out)
+{
+    if (nx <= 0 || ny <= 0 || !(radius > 0.0)) return -1;
+    double r2 = radius * radius;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double dx = (double)x - xc;
+            double dy = (double)y - yc;
+            out[(long)y * nx + x] = dx * dx + dy * dy <= r2;
+        }
+    return 0;
+}
+
 /* Neighbour x + c_i of node (x, y).  y wraps; x wraps only when periodic_x.
  * Returns -1 when the neighbour lies outside the domain in x. */
 static long neighbour(int nx, int ny, int periodic_x, int x, int y, int i)

@@ -64,6 +64,14 @@ DIFF = Workload("naca0012_512x256_c64_a2_re200_f32", 512, 256, 64.0, 0.12, 2.0, 
 WORKLOADS = {w.name: w for w in (SMALL_F64, LARGE_F32, PRECISION, DIFF)}
 
 
+def cylinder(d: int, re: float = 100.0, storage: str = "f32", steps: int = 0) -> Workload:
+    """Section VI: flow past a circular cylinder of diameter d (the `chord`
+    field) at Re = u_in d / nu; domain 60 d x 5 d, centre 15 d from the inlet
+    on the mid-line y = (ny - 1)/2 (Section VI's 12:1 aspect ratio)."""
+    return Workload("cylinder_d%d_re%g" % (d, re), 60 * d, 5 * d, float(d), 0.0, 0.0, 15.0 * d, re,
+                    steps, storage, extra={"body": "cylinder"})
+
+
 def scaled(w: Workload, factor: int, storage: str = None) -> Workload:
     """The same geometry shrunk by an integer factor (for oracle-sized cases)."""
     return Workload(w.name + "_div%d" % factor, w.nx // factor, w.ny // factor,
