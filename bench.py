@@ -352,7 +352,7 @@ def run_ours(a):
            "includes": "lbm_create from a pinned host mask, lbm_step(K), force series of all "
                        "four schemes read back, final populations read back, lbm_destroy"}
 
-    variants = adjoint = batch = None
+    variants = adjoint = batch = cyl = None
     if not a.no_variants and rank == 0:
         variants = [variant(torch, binding, w, "f64", 1000, peak, local),
                     variant(torch, binding, w, "f32dev", 4000, peak, local),
@@ -363,6 +363,10 @@ def run_ours(a):
                    adjoint_variant(torch, binding, w, "f32", 1000, 500, local)]
         batch = [batch_variant(torch, binding, inputs, 256, "f32", 2000, peak, local),
                  batch_variant(torch, binding, inputs, 256, "f16dev", 2000, peak, local)]
+        from paper_2210_10377_gb300 import cylinder
+        t0 = time.perf_counter()
+        cyl = cylinder.cd_study(device=local)
+        cyl["wall_s"] = round(time.perf_counter() - t0, 2)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -398,6 +402,7 @@ def run_ours(a):
             "variants": variants,
             "adjoint": adjoint,
             "batch": batch,
+            "cylinder": cyl,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

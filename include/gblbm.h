@@ -195,6 +195,13 @@ lbm_status lbm_control_volume(lbm_ctx *h, int *cv);
 lbm_status lbm_naca_mask(int nx, int ny, double chord, double thickness, double alpha_deg,
                          double xc, double yc, int closed_te, uint8_t *out);
 
+/* Voxelised circular cylinder of diameter D centred at (xc, yc) (Section VI,
+ * flow past a 2-D circular cylinder): out[y][x] = 1 iff
+ * (x - xc)^2 + (y - yc)^2 <= (D/2)^2, evaluated as written with separately
+ * rounded FP64 operations (bit-for-bit reproducible).  Runs on the device.
+ * EINVAL: nx, ny <= 0, D <= 0, non-finite arguments, out NULL. */
+lbm_status lbm_cylinder_mask(int nx, int ny, double xc, double yc, double diameter, uint8_t *out);
+
 /* Discrete adjoint (channel set-up, no body force, record_series = 1).
  * From the current state (step T0) run `steps` steps as lbm_step would (the
  * handle ends at T0 + steps with its force series), and return the objective

@@ -114,6 +114,8 @@ def lib():
     L.lbm_batch_launch_count.restype = C.c_longlong
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_cylinder_mask.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_uint8)]
+    L.lbm_cylinder_mask.restype = C.c_int
     L.lbm_pressure_coefficient.argtypes = [vp, C.c_double, C.c_double, C.POINTER(C.c_int32), dp, C.c_long, lp]
     L.lbm_pressure_coefficient.restype = C.c_int
     L.lbm_batch_pressure_coefficient.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int32), dp,
@@ -154,6 +156,21 @@ def naca_mask(nx, ny, chord, thickness, alpha_deg, xc, yc, closed_te=False):
                                float(alpha_deg), float(xc), float(yc), int(closed_te),
                                out.ctypes.data_as(C.POINTER(C.c_uint8))))
     return out
+
+
+def cylinder_mask(nx, ny, xc, yc, diameter):
+    """Circular cylinder voxelised on the device; uint8 [ny][nx], 1 = solid."""
+    out = np.zeros((ny, nx), np.uint8)
+    _check(lib().lbm_cylinder_mask(int(nx), int(ny), float(xc), float(yc), float(diameter),
+                                   out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return out
+
+
+def body_mask(w):
+    """The mask of a workload: its NACA section, or its cylinder."""
+    if w.extra.get("body") == "cylinder":
+        return cylinder_mask(w.nx, w.ny, w.xc, w.yc, w.chord)
+    return naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
 
 
 class _TorchAllocator:

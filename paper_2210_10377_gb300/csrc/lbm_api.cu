@@ -861,6 +861,25 @@ lbm_status lbm_naca_mask(int nx, int ny, double chord, double thickness, double 
     return LBM_OK;
 }
 
+lbm_status lbm_cylinder_mask(int nx, int ny, double xc, double yc, double diameter, uint8_t *out)
+{
+    if (nx <= 0 || ny <= 0 || !(diameter > 0) || !std::isfinite(diameter) || !out || !std::isfinite(xc) ||
+        !std::isfinite(yc))
+        return set_err(nullptr, LBM_EINVAL, "bad cylinder arguments");
+    const size_t N = (size_t)nx * ny;
+    uint8_t *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, N);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_err(nullptr, e, "cudaMalloc mask");
+    }
+    e = launch_cylinder_mask(d, nx, ny, xc, yc, 0.5 * diameter, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, N, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_err(nullptr, e, "cylinder mask");
+    return LBM_OK;
+}
+
 lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, int checkpoint_every,
                        double *J, double *dJ_dtau, double *dJ_du, double *dJ_df0)
 {

@@ -154,6 +154,8 @@ void set_thread_error(const char *msg);
 cudaError_t launch_naca_mask(uint8_t *mask, int nx, int ny, double chord, double thickness,
                              double ca, double sa, double xc, double yc, int closed_te,
                              cudaStream_t st);
+cudaError_t launch_cylinder_mask(uint8_t *mask, int nx, int ny, double xc, double yc, double radius,
+                                 cudaStream_t st);
 cudaError_t launch_node_bits(const uint8_t *mask, uint16_t *nbits, int nx, int ny, int pitch,
                              int periodic, cudaStream_t st);
 cudaError_t launch_link_count(const uint16_t *nbits, int nx, int ny, int pitch, int *block_cnt,

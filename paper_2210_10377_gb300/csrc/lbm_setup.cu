@@ -42,6 +42,28 @@ __global__ void k_naca_mask(uint8_t *__restrict__ mask, int nx, int ny, double c
     mask[n] = solid;
 }
 
+// Circular cylinder (Section VI): solid iff dx*dx + dy*dy <= r*r, with
+// separately rounded FP64 operations in that order (no contraction), so the
+// mask matches a plain C evaluation bit for bit.
+__global__ void k_cylinder_mask(uint8_t *__restrict__ mask, int nx, int ny, double xc, double yc, double r2)
+{
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (long long)nx * ny) return;
+    const int x = (int)(n % nx), y = (int)(n / nx);
+    const double dx = __dsub_rn((double)x, xc);
+    const double dy = __dsub_rn((double)y, yc);
+    mask[n] = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
+}
+
+cudaError_t launch_cylinder_mask(uint8_t *mask, int nx, int ny, double xc, double yc, double radius,
+                                 cudaStream_t st)
+{
+    const long long N = (long long)nx * ny;
+    const int blocks = (int)((N + 255) / 256);
+    k_cylinder_mask<<<blocks, 256, 0, st>>>(mask, nx, ny, xc, yc, radius * radius);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_naca_mask(uint8_t *mask, int nx, int ny, double chord, double thickness,
                              double ca, double sa, double xc, double yc, int closed_te,
                              cudaStream_t st)
