@@ -50,6 +50,8 @@ def args_():
     p.add_argument("--batch", type=int, default=0,
                    help="profile mode: a batch of the first N domains of the 256-domain "
                         "NACA00xx recipe instead of one workload")
+    p.add_argument("--batch-launch", default=None,
+                   help="profile mode: 'shape,ctas_per_sm' for the batch instead of the tuner")
     return p.parse_args()
 
 
@@ -457,7 +459,10 @@ def run_profile(a):
         torch.cuda.set_device(0)
         ws, doms = batch_domains(binding, inputs, a.batch)
         b = binding.Batch(doms, storage=a.storage or "f32")
-        b.autotune(trials=2)
+        if a.batch_launch:
+            b.set_launch(*[int(v) for v in a.batch_launch.split(",")])
+        else:
+            b.autotune(trials=2)
         b.step(a.warmup)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
