@@ -14,67 +14,130 @@ namespace gblbm {
 // Per-node pieces shared by the two collide-stream kernels.
 // ---------------------------------------------------------------------------
 
-// BGK collision of one node: rho = R0 + sum f (R0 = rho0 for deviation storage,
-// 0 otherwise), u = (sum c f)/rho, and with theta0 = 1/3 the second-order
-// equilibrium of Section II, less the base w_i R0,
-//   feq_i - w_i R0 = w_i (drho + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u^2)),
-// evaluated for opposite directions together: they share the even part
-// s = drho - 1.5 rho u^2 + 4.5 rho (c.u)^2 and differ in the sign of the odd
-// part 3 rho c.u.  ft = f + (feq - f)/tau, plus 3 w_i c_i.g with a body force.
-// out receives ft rounded to the storage type (the values that are stored).
-__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
-__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
+// BGK collision (Section II, Eq. CollideAdv): rho = R0 + sum g (R0 = rho0 for
+// deviation storage, g = f - w rho0; R0 = 0 and g = f otherwise), u = (sum c g)
+// / rho, and with theta0 = 1/3 the second-order equilibrium less its base,
+//   feq_i - w_i R0 = w_i (base + 4.5 rho (c_i.u)^2 + 3 rho c_i.u),
+//   base = drho - 1.5 rho u^2,
+// evaluated for opposite directions together (they share the even part and
+// differ in the sign of the odd one).  The relaxation ft = f + omega (feq - f)
+// is written as (1 - omega) g + (omega w_i)(even +- odd), plus 3 w_i c_i.g with
+// a body force.
+//
+// The arithmetic is spelled out operation by operation, each rounded once, in
+// one template over the value type: one node (float, double) or two nodes at
+// once in the packed FP32 pairs of this GPU (float2, two results per
+// instruction).  A subtraction of packed pairs is an fma with -1, which is
+// exact, so every lane of the packed form computes exactly the bits of the
+// one-node form: which form a node takes (a pair of rows in interior tiles,
+// single nodes elsewhere) never changes its result.
+template <typename V> struct Arith;
+template <> struct Arith<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float splat(float c) { return c; }
+    static __device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+};
+template <> struct Arith<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double splat(double c) { return c; }
+    static __device__ __forceinline__ double rcp(double v) { return __drcp_rn(v); }
+};
+template <> struct Arith<float2> {
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b)
+    {
+        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 splat(float c) { return make_float2(c, c); }
+    static __device__ __forceinline__ float2 rcp(float2 v) { return make_float2(__frcp_rn(v.x), __frcp_rn(v.y)); }
+};
 
+// One pair of opposite directions with c.u = c: even part se = base +
+// 4.5 rho c^2, odd part so = 3 rho c; vp, vm the relaxed populations.
+template <typename V>
+__device__ __forceinline__ void relax_pair(V c, V ow, V omc, V r45, V r3, V base, V gp, V gm, V &vp, V &vm)
+{
+    using O = Arith<V>;
+    const V se = O::fma(O::mul(r45, c), c, base), so = O::mul(r3, c);
+    vp = O::fma(ow, O::add(se, so), O::mul(omc, gp));
+    vm = O::fma(ow, O::sub(se, so), O::mul(omc, gm));
+}
+
+// The collision of one node (V = T) or of two (V = float2, T = float); T is
+// the compute type of the uniform constants.  rho receives the density.
+template <typename V, typename T, bool DEV, bool FORCE>
+__device__ __forceinline__ void collide_core(const StepArgs &a, const V (&g)[9], V (&v)[9], V &rho)
+{
+    using O = Arith<V>;
+    const T om = param<T>(a.omega, a.omega_f);
+    // uniform constants, the same scalar operations in every form
+    const V omc = O::splat(T(1) - om);
+    const V ow0 = O::splat(om * wgt<T>(0)), ow1 = O::splat(om * wgt<T>(1)), ow5 = O::splat(om * wgt<T>(5));
+    const V jx = O::add(O::add(O::sub(g[1], g[3]), O::sub(g[5], g[6])), O::sub(g[8], g[7]));
+    const V jy = O::sub(O::add(O::sub(g[2], g[4]), O::add(g[5], g[6])), O::add(g[7], g[8]));
+    const V drho = O::add(O::add(O::add(O::add(g[0], g[1]), O::add(g[2], g[3])),
+                                 O::add(O::add(g[4], g[5]), O::add(g[6], g[7]))),
+                          g[8]);
+    rho = DEV ? O::add(O::splat(param<T>(a.rho0, a.rho0_f)), drho) : drho;
+    const V inv = O::rcp(rho);
+    const V ux = O::mul(jx, inv), uy = O::mul(jy, inv);
+    const V usq = O::fma(ux, ux, O::mul(uy, uy));
+    const V base = O::fma(O::mul(rho, usq), O::splat(T(-1.5)), drho);
+    const V r45 = O::mul(rho, O::splat(T(4.5))), r3 = O::mul(rho, O::splat(T(3)));
+    v[0] = O::fma(ow0, base, O::mul(omc, g[0]));
+    // directions 1 (+x) and 3 (-x): c.u = ux; 2 (+y) and 4 (-y): c.u = uy;
+    // 5 (+x+y) and 7 (-x-y): ux + uy; 6 (-x+y) and 8 (+x-y): uy - ux
+    relax_pair<V>(ux, ow1, omc, r45, r3, base, g[1], g[3], v[1], v[3]);
+    relax_pair<V>(uy, ow1, omc, r45, r3, base, g[2], g[4], v[2], v[4]);
+    relax_pair<V>(O::add(ux, uy), ow5, omc, r45, r3, base, g[5], g[7], v[5], v[7]);
+    relax_pair<V>(O::sub(uy, ux), ow5, omc, r45, r3, base, g[6], g[8], v[6], v[8]);
+    if constexpr (FORCE) {
+        const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            v[i] = O::add(v[i], O::splat(T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy)));
+    }
+}
+
+// One node; out receives ft rounded to the storage type (the stored values).
 template <int S, bool FORCE>
 __device__ __forceinline__ void collide_node(const StepArgs &a, const typename Traits<S>::comp_t (&g)[9],
                                              typename Traits<S>::store_t (&out)[9], bool &bad)
 {
     using ST = typename Traits<S>::store_t;
     using T = typename Traits<S>::comp_t;
-    constexpr bool DEV = Traits<S>::dev;
-    const T R0 = DEV ? param<T>(a.rho0, a.rho0_f) : T(0);
-    const T jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
-    const T jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
-    const T drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
-    const T rho = R0 + drho;
+    T v[9], rho;
+    collide_core<T, T, Traits<S>::dev, FORCE>(a, g, v, rho);
     if (!(rho > T(0))) bad = true;
-    const T inv = recip(rho);
-    const T ux = jx * inv, uy = jy * inv;
-    const T base = drho - rho * (T(1.5) * (ux * ux + uy * uy));
-    const T r45 = T(4.5) * rho, r3 = T(3) * rho;
-    const T om = param<T>(a.omega, a.omega_f);
-    const T w0 = wgt<T>(0), w1 = wgt<T>(1), w5 = wgt<T>(5);
-    T v[9];
-    v[0] = g[0] + om * (w0 * base - g[0]);
-    {  // directions 1 (+x) and 3 (-x): c.u = ux
-        const T se = base + r45 * ux * ux, so = r3 * ux;
-        v[1] = g[1] + om * (w1 * (se + so) - g[1]);
-        v[3] = g[3] + om * (w1 * (se - so) - g[3]);
-    }
-    {  // directions 2 (+y) and 4 (-y): c.u = uy
-        const T se = base + r45 * uy * uy, so = r3 * uy;
-        v[2] = g[2] + om * (w1 * (se + so) - g[2]);
-        v[4] = g[4] + om * (w1 * (se - so) - g[4]);
-    }
-    {  // directions 5 (+x+y) and 7 (-x-y): c.u = ux + uy
-        const T c = ux + uy;
-        const T se = base + r45 * c * c, so = r3 * c;
-        v[5] = g[5] + om * (w5 * (se + so) - g[5]);
-        v[7] = g[7] + om * (w5 * (se - so) - g[7]);
-    }
-    {  // directions 6 (-x+y) and 8 (+x-y): c.u = uy - ux
-        const T c = uy - ux;
-        const T se = base + r45 * c * c, so = r3 * c;
-        v[6] = g[6] + om * (w5 * (se + so) - g[6]);
-        v[8] = g[8] + om * (w5 * (se - so) - g[8]);
-    }
-    if (FORCE) {
-        const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) v[i] += T(3) * wgt<T>(i) * (T(cx(i)) * gx + T(cy(i)) * gy);
-    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i] = to_store<ST>(v[i]);
+}
+
+// Two nodes in packed FP32 pairs (FP32 compute types only).
+template <int S, bool FORCE>
+__device__ __forceinline__ void collide_pair(const StepArgs &a, const float (&g0)[9], const float (&g1)[9],
+                                             typename Traits<S>::store_t (&out0)[9],
+                                             typename Traits<S>::store_t (&out1)[9], bool &bad)
+{
+    using ST = typename Traits<S>::store_t;
+    float2 g[9], v[9], rho;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = make_float2(g0[i], g1[i]);
+    collide_core<float2, float, Traits<S>::dev, FORCE>(a, g, v, rho);
+    if (!(rho.x > 0.0f) || !(rho.y > 0.0f)) bad = true;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        out0[i] = to_store<ST>(v[i].x);
+        out1[i] = to_store<ST>(v[i].y);
+    }
 }
 
 // Control-volume contributions of one fluid node (x, y).
@@ -110,7 +173,7 @@ __device__ __forceinline__ void cv_node(const StepArgs &a, int x, int y,
             }
         }
     }
-    if (MOMENTUM_ONLY) return;
+    if constexpr (MOMENTUM_ONLY) return;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int x2 = x + cx(i);
@@ -259,6 +322,32 @@ __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x,
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             f[r][i] = to_comp(b[r * pitch + i * plane - cy(i) * pitch - cx(i)]);
+    constexpr bool PAIRS = sizeof(T) == 4 && RPT % 2 == 0 && !MOMENTUM_ONLY;
+    if constexpr (PAIRS) {
+      if (!inlet) {
+        // two rows at a time in packed FP32 pairs (identical bits to one node at a time)
+#pragma unroll
+        for (int r = 0; r < RPT; r += 2) {
+            ST out0[9], out1[9];
+            collide_pair<S, FORCE>(a, f[r], f[r + 1], out0, out1, bad);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                o[r * pitch + i * plane] = out0[i];
+                o[(r + 1) * pitch + i * plane] = out1[i];
+            }
+            if (cvtile) {
+                T ftr[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) ftr[i] = to_comp(out0[i]);
+                cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r, f[r], ftr, 0, acc);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) ftr[i] = to_comp(out1[i]);
+                cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r + 1, f[r + 1], ftr, 0, acc);
+            }
+        }
+        return;
+      }
+    }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         T ftr[9];
