@@ -15,9 +15,10 @@ namespace gblbm {
 
 // Minimum resident CTAs per SM asked of the compiler for the one-CTA-per-tile
 // form (0: no bound), per storage: 2 x 512 threads (64 registers) for FP32,
-// 6 x 128 for FP16 deviations.  The persistent form carries no bound: its
-// tile loop keeps the domain arguments live across tiles and needs about 128
-// registers a thread.
+// 4 x 256 for FP16 deviations (1024-node tiles; both measured best with the
+// packed collision).  The persistent form carries no bound: its tile loop
+// keeps the domain arguments live across tiles and needs about 128 registers
+// a thread.
 #ifndef GBLBM_BATCH_MINB_F64
 #define GBLBM_BATCH_MINB_F64 0
 #endif
@@ -25,7 +26,7 @@ namespace gblbm {
 #define GBLBM_BATCH_MINB_F32 2
 #endif
 #ifndef GBLBM_BATCH_MINB_F16
-#define GBLBM_BATCH_MINB_F16 6
+#define GBLBM_BATCH_MINB_F16 4
 #endif
 template <int S> struct BatchMinBlocks {
     static constexpr int value = S == LBM_F64       ? GBLBM_BATCH_MINB_F64

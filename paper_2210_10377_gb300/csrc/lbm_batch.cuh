@@ -27,9 +27,14 @@ namespace gblbm {
 #endif
 constexpr int BATCH_SHAPES = 3;
 __host__ __device__ constexpr int batch_tx(int shape) { return shape == 0 ? 128 : (shape == 1 ? 64 : 32); }
+// FP16 deviations: 8-row tiles at 128 wide (1024 nodes, as FP32), so the
+// per-tile domain look-up is spread over as many nodes
+#ifndef GBLBM_BATCH_ROWS_F16
+#define GBLBM_BATCH_ROWS_F16 8
+#endif
 __host__ __device__ constexpr int batch_tr(int storage, int shape)
 {
-    return tile_rows(storage) * (128 / batch_tx(shape)) /
+    return (storage == LBM_F16_DEV ? GBLBM_BATCH_ROWS_F16 : tile_rows(storage)) * (128 / batch_tx(shape)) /
            ((storage == LBM_F32 || storage == LBM_F32_DEV) ? GBLBM_BATCH_TRDIV : 1);
 }
 __host__ __device__ constexpr int batch_rpt(int storage)
