@@ -197,11 +197,10 @@ StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
     a.periodic = h->periodic;
     a.precollision = precollision;
     a.tiles_x = h->tiles_x;
-    a.omega = h->omega;
+    set_relaxation(a, h->omega);
     a.rho0 = h->rho0;
     a.gx = h->g[0];
     a.gy = h->g[1];
-    a.omega_f = (float)h->omega;
     a.rho0_f = (float)h->rho0;
     a.gx_f = (float)h->g[0];
     a.gy_f = (float)h->g[1];

@@ -77,10 +77,9 @@ __device__ __forceinline__ void batch_tile(const BatchParams &p, int k)
         a.precollision = p.precollision;
         a.tiles_x = m.tiles_x;
         a.tile_off_x = a.tile_off_y = 0;
-        a.omega = m.omega;
+        set_relaxation(a, m.omega);
         a.rho0 = p.rho0;
         a.gx = a.gy = 0.0;
-        a.omega_f = (float)m.omega;
         a.rho0_f = p.rho0_f;
         a.gx_f = a.gy_f = 0.0f;
 #pragma unroll

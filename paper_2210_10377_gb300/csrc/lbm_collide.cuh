@@ -24,10 +24,10 @@ namespace gblbm {
 // is written as (1 - omega) g + (omega w_i)(even +- odd), plus 3 w_i c_i.g with
 // a body force.
 //
-// The arithmetic is spelled out operation by operation, each rounded once, in
-// one template over the value type: one node (float, double) or two nodes at
+// The FP32 arithmetic is spelled out operation by operation, each rounded
+// once, in one template over the value type: one node (float) or two nodes at
 // once in the packed FP32 pairs of this GPU (float2, two results per
-// instruction).  A subtraction of packed pairs is an fma with -1, which is
+// instruction); FP64 (double) runs the same expression.  A subtraction of packed pairs is an fma with -1, which is
 // exact, so every lane of the packed form computes exactly the bits of the
 // one-node form: which form a node takes (a pair of rows in interior tiles,
 // single nodes elsewhere) never changes its result.
@@ -40,13 +40,15 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float splat(float c) { return c; }
     static __device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
 };
+// FP64 has no packed form, so its operations are left to the compiler (it
+// may fuse a product into the following sum), as in any FP64 expression.
 template <> struct Arith<double> {
-    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+    static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return a * b + c; }
     static __device__ __forceinline__ double splat(double c) { return c; }
-    static __device__ __forceinline__ double rcp(double v) { return __drcp_rn(v); }
+    static __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
 };
 template <> struct Arith<float2> {
     static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -77,10 +79,10 @@ template <typename V, typename T, bool DEV, bool FORCE>
 __device__ __forceinline__ void collide_core(const StepArgs &a, const V (&g)[9], V (&v)[9], V &rho)
 {
     using O = Arith<V>;
-    const T om = param<T>(a.omega, a.omega_f);
-    // uniform constants, the same scalar operations in every form
-    const V omc = O::splat(T(1) - om);
-    const V ow0 = O::splat(om * wgt<T>(0)), ow1 = O::splat(om * wgt<T>(1)), ow5 = O::splat(om * wgt<T>(5));
+    // uniform constants 1 - omega and omega w_i, computed once per launch
+    const V omc = O::splat(param<T>(a.omc, a.omc_f));
+    const V ow0 = O::splat(param<T>(a.ow[0], a.ow_f[0])), ow1 = O::splat(param<T>(a.ow[1], a.ow_f[1]));
+    const V ow5 = O::splat(param<T>(a.ow[2], a.ow_f[2]));
     const V jx = O::add(O::add(O::sub(g[1], g[3]), O::sub(g[5], g[6])), O::sub(g[8], g[7]));
     const V jy = O::sub(O::add(O::sub(g[2], g[4]), O::add(g[5], g[6])), O::add(g[7], g[8]));
     const V drho = O::add(O::add(O::add(O::add(g[0], g[1]), O::add(g[2], g[3])),

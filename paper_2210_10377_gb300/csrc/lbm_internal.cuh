@@ -115,11 +115,27 @@ struct StepArgs {
     int tile_off_x, tile_off_y;  // added to blockIdx (momentum-only pass)
     double omega, rho0, gx, gy;
     float omega_f, rho0_f, gx_f, gy_f;  // the same in FP32 (no FP64 conversions in FP32 kernels)
+    double omc, ow[3];       // 1 - omega and omega w_i for w = 4/9, 1/9, 1/36 (set_relaxation)
+    float omc_f, ow_f[3];    // the same rounded to FP32
     int cv[4];               // inclusive control-volume box
     int cvt[4];              // inclusive tile rectangle holding the box and its halo
     int use_bulk;            // staged (TMA) kernel allowed (channel set-up, pulled state)
     int sm_count;            // persistent grid size of the staged kernel
 };
+
+// The relaxation constants of a StepArgs, from omega: computed in FP64 in a
+// fixed order (host and device give the same bits), then rounded to FP32.
+__host__ __device__ inline void set_relaxation(StepArgs &a, double omega)
+{
+    a.omega = omega;
+    a.omega_f = (float)omega;
+    a.omc = 1.0 - omega;
+    a.ow[0] = omega * (4.0 / 9.0);
+    a.ow[1] = omega * (1.0 / 9.0);
+    a.ow[2] = omega * (1.0 / 36.0);
+    a.omc_f = (float)a.omc;
+    for (int k = 0; k < 3; ++k) a.ow_f[k] = (float)a.ow[k];
+}
 
 struct LinkArgs {
     const void *src, *dst;
