@@ -77,7 +77,10 @@ __device__ __forceinline__ void batch_tile(const BatchParams &p, int k)
         a.precollision = p.precollision;
         a.tiles_x = m.tiles_x;
         a.tile_off_x = a.tile_off_y = 0;
-        set_relaxation(a, m.omega);
+        if constexpr (S == LBM_F64)
+            set_relaxation_f64(a, m.omega);
+        else
+            set_relaxation_f32(a, (float)m.omega);
         a.rho0 = p.rho0;
         a.gx = a.gy = 0.0;
         a.rho0_f = p.rho0_f;

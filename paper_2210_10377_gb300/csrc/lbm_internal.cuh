@@ -123,18 +123,30 @@ struct StepArgs {
     int sm_count;            // persistent grid size of the staged kernel
 };
 
-// The relaxation constants of a StepArgs, from omega: computed in FP64 in a
-// fixed order (host and device give the same bits), then rounded to FP32.
-__host__ __device__ inline void set_relaxation(StepArgs &a, double omega)
+// The relaxation constants of a StepArgs, from omega: the FP64 set in FP64
+// and the FP32 set in FP32 from the rounded omega, each in a fixed order, so
+// host and device give the same bits.  A kernel fills in only the set its
+// storage computes with (the FP32 kernels do no FP64 arithmetic for it).
+__host__ __device__ inline void set_relaxation_f64(StepArgs &a, double omega)
 {
     a.omega = omega;
-    a.omega_f = (float)omega;
     a.omc = 1.0 - omega;
     a.ow[0] = omega * (4.0 / 9.0);
     a.ow[1] = omega * (1.0 / 9.0);
     a.ow[2] = omega * (1.0 / 36.0);
-    a.omc_f = (float)a.omc;
-    for (int k = 0; k < 3; ++k) a.ow_f[k] = (float)a.ow[k];
+}
+__host__ __device__ inline void set_relaxation_f32(StepArgs &a, float omega)
+{
+    a.omega_f = omega;
+    a.omc_f = 1.0f - omega;
+    a.ow_f[0] = omega * (4.0f / 9.0f);
+    a.ow_f[1] = omega * (1.0f / 9.0f);
+    a.ow_f[2] = omega * (1.0f / 36.0f);
+}
+__host__ inline void set_relaxation(StepArgs &a, double omega)
+{
+    set_relaxation_f64(a, omega);
+    set_relaxation_f32(a, (float)omega);
 }
 
 struct LinkArgs {
