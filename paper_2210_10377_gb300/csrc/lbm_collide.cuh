@@ -123,6 +123,23 @@ __device__ __forceinline__ void collide_node(const StepArgs &a, const typename T
     for (int i = 0; i < 9; ++i) out[i] = to_store<ST>(v[i]);
 }
 
+// Two nodes in packed FP32 pairs from their populations already paired.
+template <int S, bool FORCE>
+__device__ __forceinline__ void collide_pair2(const StepArgs &a, const float2 (&g)[9],
+                                              typename Traits<S>::store_t (&out0)[9],
+                                              typename Traits<S>::store_t (&out1)[9], bool &bad)
+{
+    using ST = typename Traits<S>::store_t;
+    float2 v[9], rho;
+    collide_core<float2, float, Traits<S>::dev, FORCE>(a, g, v, rho);
+    if (!(rho.x > 0.0f) || !(rho.y > 0.0f)) bad = true;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        out0[i] = to_store<ST>(v[i].x);
+        out1[i] = to_store<ST>(v[i].y);
+    }
+}
+
 // Two nodes in packed FP32 pairs (FP32 compute types only).
 template <int S, bool FORCE>
 __device__ __forceinline__ void collide_pair(const StepArgs &a, const float (&g0)[9], const float (&g1)[9],
@@ -318,6 +335,48 @@ __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x,
     const int xs = x == a.nx - 1 ? x - 1 : x;
     const ST *__restrict__ b = (const ST *)a.src + (long long)y0 * pitch + xs;
     ST *__restrict__ o = (ST *)a.dst + (long long)y0 * pitch + x;
+    if constexpr (S == LBM_F16_DEV && RPT % 2 == 0 && !MOMENTUM_ONLY) {
+        if (!inlet) {
+            // FP16 deviations: the populations of a thread's row pairs are held
+            // packed two to a register until the pair collision widens them
+            __half2 h[RPT / 2][9];
+#pragma unroll
+            for (int q = 0; q < RPT / 2; ++q)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const long long off = i * plane - cy(i) * pitch - cx(i);
+                    h[q][i] = __halves2half2(b[(2 * q) * pitch + off], b[(2 * q + 1) * pitch + off]);
+                }
+#pragma unroll
+            for (int q = 0; q < RPT / 2; ++q) {
+                float2 g[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = __half22float2(h[q][i]);
+                ST out0[9], out1[9];
+                collide_pair2<S, FORCE>(a, g, out0, out1, bad);
+                const int r = 2 * q;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    o[r * pitch + i * plane] = out0[i];
+                    o[(r + 1) * pitch + i * plane] = out1[i];
+                }
+                if (cvtile) {
+                    T f0[9], f1[9], ftr[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        f0[i] = g[i].x;
+                        f1[i] = g[i].y;
+                        ftr[i] = to_comp(out0[i]);
+                    }
+                    cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r, f0, ftr, 0, acc);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) ftr[i] = to_comp(out1[i]);
+                    cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r + 1, f1, ftr, 0, acc);
+                }
+            }
+            return;
+        }
+    }
     T f[RPT][9];
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
