@@ -7,7 +7,7 @@
 // The grid is persistent (a multiple of the SM count, chosen by the host's
 // tuner) or one CTA per tile; each CTA walks the launch's tiles with a stride
 // of the grid size.  Per tile it finds the tile's domain in the kernel
-// parameter block and runs the tile.
+// parameter block (the tile table names it) and runs the tile.
 #include "lbm_batch.cuh"
 #include "lbm_collide.cuh"
 
@@ -34,21 +34,6 @@ template <int S> struct BatchMinBlocks {
                                                     : GBLBM_BATCH_MINB_F32;
 };
 
-// The domain of tile k: the last domain whose first tile is <= k (binary
-// search; k and the table are block-uniform).
-__device__ __forceinline__ int domain_of(const BatchParams &p, int k)
-{
-    int lo = 0, hi = p.n_dom - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.dom[mid].tile_start <= k)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
 // Tile k of the launch: its domain's arguments, its place in the domain, and
 // the single-domain tile body.
 template <int S, bool MOMENTUM_ONLY, int TX, int TR, int RPT>
@@ -57,7 +42,9 @@ __device__ __forceinline__ void batch_tile(const BatchParams &p, int k)
     static_assert(TR % RPT == 0, "rows per thread must divide the tile rows");
     const long long elem = (long long)sizeof(typename Traits<S>::store_t);
     {
-        const int d = domain_of(p, k);
+        // the tile's entry: domain (within the launch), tile column, tile row, checked
+        const int4 e = __ldg(p.tiles + k);
+        const int d = e.x;
         const BatchDomain &m = p.dom[d];
         StepArgs a;
         a.src = p.src + (long long)m.pop_off64 * 64 * elem;
@@ -92,17 +79,7 @@ __device__ __forceinline__ void batch_tile(const BatchParams &p, int k)
         }
         a.use_bulk = 0;
         a.sm_count = 0;
-        const int r = k - m.tile_start;
-        int tx, ty;
-        if (p.cv_only) {  // the tiles of the control-volume rectangle, row by row
-            const int w = m.cvt[1] - m.cvt[0] + 1;
-            tx = m.cvt[0] + r % w;
-            ty = m.cvt[2] + r / w;
-        } else {
-            tx = r % m.tiles_x;
-            ty = r / m.tiles_x;
-        }
-        collide_tile<S, MOMENTUM_ONLY, false, TX, TR, RPT>(a, tx, ty, p.precollision || p.checked[k] != 0);
+        collide_tile<S, MOMENTUM_ONLY, false, TX, TR, RPT>(a, e.y, e.z, p.precollision || e.w != 0);
     }
 }
 

@@ -4,10 +4,9 @@
 //
 // Every domain keeps the single-domain layout ([9][ny][pitch] planes of the
 // storage type) at its own offset in two shared population arenas.  The
-// collide-stream kernel numbers the tiles of all domains of a launch domain by
-// domain; a CTA finds the domain of its tile by a binary search over the
-// domains' first tiles, a block-uniform computation on the kernel parameter,
-// so the domain's arguments stay in uniform registers.  The link kernel runs
+// collide-stream kernel walks a table of the tiles of all domains of a launch,
+// domain by domain; a tile's entry names its domain, whose arguments come from
+// the kernel parameter (block-uniform reads of the constant bank).  The link kernel runs
 // one CTA per domain.
 #pragma once
 
@@ -52,7 +51,6 @@ struct BatchDomain {
     int node_off64;   // neighbour-bit arena offset / 64
     int inlet_off64;  // inlet arena offset / 64 (elements)
     int part_off;     // first partial row of the domain (this tile shape)
-    int tile_start;   // first tile of the domain in the launch's tile order
     int nx, ny;       // grid (nx, ny <= 32767); the pitch is nx rounded up to 64
     int tiles_x;      // tiles per row (this tile shape)
     short cv[4];      // control volume, inclusive
@@ -74,7 +72,8 @@ struct BatchParams {
     double *partials;        // control-volume partial rows
     int *status;             // [domain][2] of the whole batch
     const long long *step_ctr;
-    const uint8_t *checked;  // per tile of the launch's order: 1 = bounce-back-aware path
+    const int4 *tiles;       // per tile of the launch: {domain within the launch, tx, ty,
+                             // 1 = bounce-back-aware path}
     int n_dom;               // domains in this chunk
     int dom_base;            // index of the chunk's first domain in the batch (status rows)
     int n_tiles;             // tiles of this launch

@@ -73,9 +73,9 @@ struct lbm_batch {
     int32_t *bnodes = nullptr;        // boundary fluid nodes of every domain, at its link offset
     double *partials = nullptr;       // [max over shapes of the partial rows][CV_PARTIAL]
     double *tune_partials = nullptr;  // the tuner's scratch copy of it
-    uint8_t *checked[BATCH_SHAPES] = {nullptr, nullptr, nullptr};     // per tile, batch order
+    int4 *checked[BATCH_SHAPES] = {nullptr, nullptr, nullptr};     // tile table, batch order
     long long n_tiles[BATCH_SHAPES] = {0, 0, 0};
-    uint8_t *checked_cv[BATCH_SHAPES] = {nullptr, nullptr, nullptr};  // per control-volume tile
+    int4 *checked_cv[BATCH_SHAPES] = {nullptr, nullptr, nullptr};  // control-volume tiles
     long long n_cv_entries[BATCH_SHAPES] = {0, 0, 0};
     LinkArgs *largs = nullptr;  // [BATCH_SHAPES][3][n]: slots 0/1 = source buffer, 2 = first step (pre-collision)
     double *series = nullptr;   // [series_cap][n][SERIES_ROW]
@@ -191,7 +191,7 @@ void make_params(const lbm_batch *b, int s, int src, int c, bool cv_only, bool t
     p.n_dom = d1 - d0;
     p.dom_base = d0;
     const long long base = cv_only ? b->dom[d0].cv_base[s] : b->dom[d0].tile_base[s];
-    p.checked = (cv_only ? b->checked_cv[s] : b->checked[s]) + base;
+    p.tiles = (cv_only ? b->checked_cv[s] : b->checked[s]) + base;
     long long end = base;
     for (int d = d0; d < d1; ++d) {
         const Domain &m = b->dom[d];
@@ -201,7 +201,6 @@ void make_params(const lbm_batch *b, int s, int src, int c, bool cv_only, bool t
         q.node_off64 = (int)(m.node_off / 64);
         q.inlet_off64 = (int)(m.inlet_off / 64);
         q.part_off = (int)m.cvp_off[s];
-        q.tile_start = (int)((cv_only ? m.cv_base[s] : m.tile_base[s]) - base);
         q.nx = m.nx;
         q.ny = m.ny;
         q.tiles_x = m.tiles_x[s];
@@ -647,7 +646,7 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
         if (e != cudaSuccess) return fail(bcuda(b, e, "tile flags"));
         // per-tile flags in the batch's tile order (domain by domain, row by
         // row), and the same for the control-volume rectangles
-        std::vector<uint8_t> chk, chk_cv;
+        std::vector<int4> chk, chk_cv;
         for (int d = 0; d < n; ++d) {
             Domain &m = b->dom[d];
             const int tiles_x = (m.nx + tw - 1) / tw, tiles_y = (m.ny + th - 1) / th;
@@ -655,17 +654,21 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
             m.tile_base[sh] = (long long)chk.size();
             m.cv_base[sh] = (long long)chk_cv.size();
             for (int ty = 0; ty < tiles_y; ++ty)
-                for (int tx = 0; tx < tiles_x; ++tx) chk.push_back(flags[foff[d] + (long long)ty * tiles_x + tx] ? 1 : 0);
+                for (int tx = 0; tx < tiles_x; ++tx)
+                    chk.push_back(make_int4(d % MAX_BATCH_DOMAINS, tx, ty,
+                                            flags[foff[d] + (long long)ty * tiles_x + tx] ? 1 : 0));
             for (int ty = m.cvt[sh][2]; ty <= m.cvt[sh][3]; ++ty)
                 for (int tx = m.cvt[sh][0]; tx <= m.cvt[sh][1]; ++tx)
-                    chk_cv.push_back(flags[foff[d] + (long long)ty * tiles_x + tx] ? 1 : 0);
+                    chk_cv.push_back(make_int4(d % MAX_BATCH_DOMAINS, tx, ty,
+                                               flags[foff[d] + (long long)ty * tiles_x + tx] ? 1 : 0));
         }
         b->n_tiles[sh] = (long long)chk.size();
         b->n_cv_entries[sh] = (long long)chk_cv.size();
-        BALLOC(b->checked[sh], uint8_t *, chk.size() > 0 ? chk.size() : 1);
-        BALLOC(b->checked_cv[sh], uint8_t *, chk_cv.size() > 0 ? chk_cv.size() : 1);
-        BCKC(cudaMemcpyAsync(b->checked[sh], chk.data(), chk.size(), cudaMemcpyHostToDevice, s), "H2D tile flags");
-        BCKC(cudaMemcpyAsync(b->checked_cv[sh], chk_cv.data(), chk_cv.size(), cudaMemcpyHostToDevice, s),
+        BALLOC(b->checked[sh], int4 *, sizeof(int4) * (chk.size() > 0 ? chk.size() : 1));
+        BALLOC(b->checked_cv[sh], int4 *, sizeof(int4) * (chk_cv.size() > 0 ? chk_cv.size() : 1));
+        BCKC(cudaMemcpyAsync(b->checked[sh], chk.data(), sizeof(int4) * chk.size(), cudaMemcpyHostToDevice, s),
+             "H2D tile table");
+        BCKC(cudaMemcpyAsync(b->checked_cv[sh], chk_cv.data(), sizeof(int4) * chk_cv.size(), cudaMemcpyHostToDevice, s),
              "H2D control-volume tile flags");
         BCKC(cudaStreamSynchronize(s), "sync");
     }
