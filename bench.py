@@ -3,8 +3,8 @@
 
 One bench step is one lattice time step of the whole hot path: the fused
 collide-stream kernel over the grid (bounce-back, inlet/outlet, DRTT partials)
-plus the link kernel (momentum exchange A, A', B and DRTT), forces of every
-scheme recorded on the device.  Default workload: 4096 x 2048 NACA0012, chord
+plus the link kernel (momentum exchange A, A', B, DRTT and stress integration),
+forces of every scheme recorded on the device.  Default workload: 4096 x 2048 NACA0012, chord
 256 at 4 degrees, Re 1000, FP32 storage.  The population arrays (2 x 302 MB)
 exceed the 129 MB L2, so no flush is needed between steps.
 
@@ -369,6 +369,9 @@ def run_ours(a):
         t0 = time.perf_counter()
         cyl = cylinder.cd_study(device=local)
         cyl["wall_s"] = round(time.perf_counter() - t0, 2)
+        t0 = time.perf_counter()
+        cyl["cd_vs_re"] = cylinder.cd_vs_re(device=local)
+        cyl["cd_vs_re"]["wall_s"] = round(time.perf_counter() - t0, 2)
 
     cpu = None
     if rank == 0 and world == 1:

@@ -1,6 +1,6 @@
 """Flow past a circular cylinder (Section VI): the drag coefficient against
-grid resolution for every force scheme, and the pressure coefficient on the
-cylinder's boundary nodes.
+grid resolution and against the Reynolds number for every force scheme, and
+the pressure coefficient on the cylinder's boundary nodes.
 
 The resolutions run together as one batch of uneven domains (lbm_batch_*), so
 a whole convergence study is one sequence of batched launches.  Each domain is
@@ -53,6 +53,36 @@ def cd_study(diameters=(10, 15, 20, 30, 40), re=100.0, flow_times=100.0, window_
     flags, _ = b.status()
     out = {"re": re, "steps": steps, "window": window, "storage": storage, "rows": rows,
            "unstable_domains": int(flags.sum()), "nodes": b.nodes}
+    b.close()
+    return out
+
+
+def cd_vs_re(d=20, res=(20.0, 40.0, 60.0, 100.0, 150.0, 200.0), flow_times=100.0, window_flow_times=40.0,
+             storage="f32", device=0):
+    """Cd of every scheme against the Reynolds number at one resolution
+    (Section VI's second cylinder study): the same 60 d x 5 d geometry at each
+    Re, tau = 1/2 + 3 u_in d / Re, all run as one batch."""
+    ws = [inputs.cylinder(int(d), re) for re in res]
+    mask = binding.body_mask(ws[0])
+    doms = [{"mask": mask, "tau": w.tau, "u_in": w.u_in} for w in ws]
+    u = ws[0].u_in
+    steps = int(round(flow_times * d / u))
+    window = int(round(window_flow_times * d / u))
+    b = binding.Batch(doms, storage=storage, device=device)
+    b.autotune(trials=3)
+    b.step(steps)
+    norm = 2.0 / (ws[0].rho0 * u * u * d)
+    rows = []
+    for k, (w, re) in enumerate(zip(ws, res)):
+        row = {"Re": float(re), "tau": round(w.tau, 6)}
+        for s_ in SCHEMES:
+            fx, fy = b.force_series(k, s_, steps - window, window)
+            row["Cd_" + s_] = float(norm * abs(fx.mean()))
+            row["Cl_std_" + s_] = float(norm * fy.std())
+        rows.append(row)
+    flags, _ = b.status()
+    out = {"D": int(d), "steps": steps, "window": window, "storage": storage, "rows": rows,
+           "unstable_domains": int(flags.sum())}
     b.close()
     return out
 

@@ -57,3 +57,15 @@ def test_convergence_study_runs_and_drtt_tracks_b(gb):
         for s in cylinder.SCHEMES:
             assert np.isfinite(row["Cd_" + s]) and row["Cd_" + s] > 0, (row["D"], s)
         assert abs(row["Cd_DRTT"] - row["Cd_B"]) <= 1e-3 * row["Cd_B"], row
+
+
+def test_cd_against_reynolds_number_runs(gb):
+    from paper_2210_10377_gb300 import cylinder
+    out = cylinder.cd_vs_re(d=10, res=(40.0, 100.0), flow_times=20.0, window_flow_times=5.0)
+    assert out["unstable_domains"] == 0 and [r["Re"] for r in out["rows"]] == [40.0, 100.0]
+    for row in out["rows"]:
+        for s in cylinder.SCHEMES:
+            assert np.isfinite(row["Cd_" + s]) and row["Cd_" + s] > 0, (row["Re"], s)
+        assert abs(row["Cd_DRTT"] - row["Cd_B"]) <= 1e-3 * row["Cd_B"], row
+    # drag falls as the Reynolds number grows (viscous drag dominates at low Re)
+    assert out["rows"][0]["Cd_B"] > out["rows"][1]["Cd_B"]
