@@ -86,7 +86,7 @@ __device__ __forceinline__ void batch_tile(const BatchParams &p, int k)
 // PERSIST: a grid of a few CTAs per SM walks the tiles with a stride of the
 // grid; otherwise one CTA per tile.
 template <int S, bool MOMENTUM_ONLY, bool PERSIST, int TX, int TR, int RPT>
-__global__ void __launch_bounds__(TX *(TR / RPT), PERSIST ? 0 : BatchMinBlocks<S>::value)
+__global__ void __launch_bounds__((TX / cols_per_thread(S)) * (TR / RPT), PERSIST ? 0 : BatchMinBlocks<S>::value)
     k_collide_stream_batch(const __grid_constant__ BatchParams p)
 {
     if (PERSIST) {
@@ -102,7 +102,7 @@ struct BatchKernel {
     static void *fn() { return (void *)k_collide_stream_batch<S, MOM, PERSIST, TX, TR, RPT>; }
     static cudaError_t launch(const BatchParams &p, int grid, cudaStream_t st)
     {
-        k_collide_stream_batch<S, MOM, PERSIST, TX, TR, RPT><<<grid, dim3(TX, TR / RPT), 0, st>>>(p);
+        k_collide_stream_batch<S, MOM, PERSIST, TX, TR, RPT><<<grid, dim3(TX / cols_per_thread(S), TR / RPT), 0, st>>>(p);
         return cudaGetLastError();
     }
 };
@@ -159,7 +159,7 @@ int batch_max_ctas_per_sm(int storage, int shape)
     case LBM_F32_DEV: fn = kernel_of<LBM_F32_DEV>(shape); break;
     default: fn = kernel_of<LBM_F16_DEV>(shape); break;
     }
-    const int threads = batch_tx(shape) * (batch_tr(storage, shape) / batch_rpt(storage));
+    const int threads = (batch_tx(shape) / cols_per_thread(storage)) * (batch_tr(storage, shape) / batch_rpt(storage));
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) {
         cudaGetLastError();

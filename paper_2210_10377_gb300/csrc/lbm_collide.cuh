@@ -433,9 +433,77 @@ __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x,
     }
 }
 
+// Interior tiles of FP16 deviations, two adjacent columns x, x+1 (x even, both
+// strictly inside (0, nx-1)) and RPT rows per thread: the directions with
+// c_x = 0 load both columns as one aligned __half2, the others load their two
+// halves; the two columns collide together as the lanes of the packed pair and
+// every direction stores both as one __half2.  The same bits as one column at a
+// time.
+template <int S, bool MOMENTUM_ONLY, int RPT, bool FORCE>
+__device__ __forceinline__ void column_pair_update_interior(const StepArgs &a, int x, int y0,
+                                                            typename AccOf<S>::type (&acc)[6],
+                                                            bool cvtile, bool &bad)
+{
+    static_assert(S == LBM_F16_DEV, "column pairs are the FP16-deviation layout");
+    const long long pitch = a.pitch, plane = a.plane;
+    const __half *__restrict__ b = (const __half *)a.src + (long long)y0 * pitch + x;
+    __half *__restrict__ o = (__half *)a.dst + (long long)y0 * pitch + x;
+    __half2 h[RPT][9];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const long long off = r * pitch + i * plane - cy(i) * pitch;
+            if (cx(i) == 0)
+                h[r][i] = *(const __half2 *)(b + off);
+            else
+                h[r][i] = __halves2half2(b[off - cx(i)], b[off + 1 - cx(i)]);
+        }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        float2 g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = __half22float2(h[r][i]);
+        if constexpr (!MOMENTUM_ONLY) {
+            float2 v[9], rho;
+            collide_core<float2, float, true, FORCE>(a, g, v, rho);
+            if (!(rho.x > 0.0f) || !(rho.y > 0.0f)) bad = true;
+            __half2 out[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                out[i] = __float22half2_rn(v[i]);
+                *(__half2 *)(o + r * pitch + i * plane) = out[i];
+            }
+            if (cvtile) {
+                float f0[9], f1[9], t0[9], t1[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    f0[i] = g[i].x;
+                    f1[i] = g[i].y;
+                    const float2 w = __half22float2(out[i]);
+                    t0[i] = w.x;
+                    t1[i] = w.y;
+                }
+                cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r, f0, t0, 0, acc);
+                cv_node<S, MOMENTUM_ONLY, FORCE>(a, x + 1, y0 + r, f1, t1, 0, acc);
+            }
+        } else if (cvtile) {
+            float f0[9], f1[9], none[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f0[i] = g[i].x;
+                f1[i] = g[i].y;
+                none[i] = 0.0f;
+            }
+            cv_node<S, MOMENTUM_ONLY, FORCE>(a, x, y0 + r, f0, none, 0, acc);
+            cv_node<S, MOMENTUM_ONLY, FORCE>(a, x + 1, y0 + r, f1, none, 0, acc);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
-// One tile of TX x TR nodes with TX x (TR/RPT) threads (threadIdx.x: column,
-// threadIdx.y: group of RPT rows).  `checked` selects the bounce-back-aware
+// One tile of TX x TR nodes with (TX/COLS) x (TR/RPT) threads (threadIdx.x:
+// COLS adjacent columns, threadIdx.y: group of RPT rows).  `checked` selects the bounce-back-aware
 // path (solid nodes in or next to the tile, or a pre-collision state).  A
 // block that met rho <= 0 or NaN sets status bit 0 and the first bad step.
 // All threads of the block must call it (it synchronises).
@@ -444,7 +512,8 @@ template <int S, bool MOMENTUM_ONLY, bool FORCE, int TX, int TR, int RPT>
 __device__ __forceinline__ void collide_tile(const StepArgs &a, int tx, int ty, bool checked)
 {
     using A = typename AccOf<S>::type;
-    const int x = tx * TX + threadIdx.x;
+    constexpr int COLS = cols_per_thread(S);
+    const int x = tx * TX + COLS * threadIdx.x;
     const bool cvtile = tx >= a.cvt[0] && tx <= a.cvt[1] && ty >= a.cvt[2] && ty <= a.cvt[3];
     A acc[6];
 #pragma unroll
@@ -452,7 +521,22 @@ __device__ __forceinline__ void collide_tile(const StepArgs &a, int tx, int ty, 
     bool bad = false;
     const int y0 = ty * TR + threadIdx.y * RPT;
     const bool interior = !checked && !a.periodic && ty > 0 && (ty + 1) * TR < a.ny;
-    if (x < a.nx) {
+    if constexpr (COLS == 2) {
+        if (interior && x >= 1 && x + 1 <= a.nx - 2) {
+            column_pair_update_interior<S, MOMENTUM_ONLY, RPT, FORCE>(a, x, y0, acc, cvtile, bad);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (x + c >= a.nx) continue;
+                if (interior)
+                    column_update_interior<S, MOMENTUM_ONLY, RPT, FORCE>(a, x + c, y0, acc, cvtile, bad);
+                else if (checked)
+                    column_update<S, true, MOMENTUM_ONLY, RPT, FORCE>(a, x + c, y0, acc, cvtile, bad);
+                else
+                    column_update<S, false, MOMENTUM_ONLY, RPT, FORCE>(a, x + c, y0, acc, cvtile, bad);
+            }
+        }
+    } else if (x < a.nx) {
         if (interior)
             column_update_interior<S, MOMENTUM_ONLY, RPT, FORCE>(a, x, y0, acc, cvtile, bad);
         else if (checked)
@@ -460,7 +544,7 @@ __device__ __forceinline__ void collide_tile(const StepArgs &a, int tx, int ty, 
         else
             column_update<S, false, MOMENTUM_ONLY, RPT, FORCE>(a, x, y0, acc, cvtile, bad);
     }
-    if (cvtile) cv_store<S, MOMENTUM_ONLY, TX *(TR / RPT)>(a, tx, ty, acc);
+    if (cvtile) cv_store<S, MOMENTUM_ONLY, (TX / COLS) * (TR / RPT)>(a, tx, ty, acc);
     if (!MOMENTUM_ONLY) {
         const int any_bad = __syncthreads_or(bad);
         if (any_bad && threadIdx.x == 0 && threadIdx.y == 0) {

@@ -44,10 +44,20 @@ __host__ __device__ constexpr int tile_rows(int storage)
 {
     return (storage == LBM_F32 || storage == LBM_F32_DEV) ? 8 : 4;
 }
-// rows per thread of the direct-load kernel (enough loads in flight per thread)
+// Adjacent columns per thread of the direct-load kernels: FP16 deviations
+// take two, so that loads and stores move 4-byte pairs (a tuning knob).
+#ifndef GBLBM_COLS_F16
+#define GBLBM_COLS_F16 2
+#endif
+__host__ __device__ constexpr int cols_per_thread(int storage)
+{
+    return storage == LBM_F16_DEV ? GBLBM_COLS_F16 : 1;
+}
+// rows per thread of the direct-load kernel (enough loads in flight per thread:
+// 4 nodes a thread for FP16 deviations, 2 for FP32, 1 for FP64)
 __host__ __device__ constexpr int direct_rpt(int storage)
 {
-    return storage == LBM_F64 ? 1 : (storage == LBM_F16_DEV ? 4 : 2);
+    return storage == LBM_F64 ? 1 : (storage == LBM_F16_DEV ? 4 / GBLBM_COLS_F16 : 2);
 }
 
 // ---- D2Q9 (Section II, Table tabD2Q9) as compile-time functions ----

@@ -43,7 +43,8 @@ template <> struct DirectMinBlocks<LBM_F16_DEV> {
 // 128 x TR tile; tiles without solids away from the domain's edges take the
 // interior path (collide_tile).
 template <int S, bool MOMENTUM_ONLY, bool FORCE>
-__global__ void __launch_bounds__(TILE_X *(tile_rows(S) / direct_rpt(S)), DirectMinBlocks<S>::value)
+__global__ void __launch_bounds__((TILE_X / cols_per_thread(S)) * (tile_rows(S) / direct_rpt(S)),
+                                  DirectMinBlocks<S>::value)
     k_collide_stream(StepArgs a)
 {
     const int tx = blockIdx.x + a.tile_off_x, ty = blockIdx.y + a.tile_off_y;
@@ -342,7 +343,7 @@ cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, i
     }
     dim3 grid(tiles_x, tiles_y);
     const bool force = a.gx != 0.0 || a.gy != 0.0;
-    dim3 block(TILE_X, tile_rows(storage) / direct_rpt(storage));
+    dim3 block(TILE_X / cols_per_thread(storage), tile_rows(storage) / direct_rpt(storage));
 #define GBLBM_CS(S)                                                    \
     if (momentum_only)                                                 \
         k_collide_stream<S, true, false><<<grid, block, 0, st>>>(a);   \
