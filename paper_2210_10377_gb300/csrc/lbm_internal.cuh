@@ -40,9 +40,13 @@ constexpr int CV_PARTIAL = 6;
 constexpr int LINK_PARTIAL = 14;
 constexpr int SERIES_ROW = 12;
 
+// Tile rows of the FP16-deviation kernels (a tuning knob).
+#ifndef GBLBM_TR_F16
+#define GBLBM_TR_F16 4
+#endif
 __host__ __device__ constexpr int tile_rows(int storage)
 {
-    return (storage == LBM_F32 || storage == LBM_F32_DEV) ? 8 : 4;
+    return (storage == LBM_F32 || storage == LBM_F32_DEV) ? 8 : (storage == LBM_F16_DEV ? GBLBM_TR_F16 : 4);
 }
 // Adjacent columns per thread of the direct-load kernels: FP16 deviations
 // take two, so that loads and stores move 4-byte pairs (a tuning knob).
@@ -55,9 +59,12 @@ __host__ __device__ constexpr int cols_per_thread(int storage)
 }
 // rows per thread of the direct-load kernel (enough loads in flight per thread:
 // 4 nodes a thread for FP16 deviations, 2 for FP32, 1 for FP64)
+#ifndef GBLBM_RPT_F16
+#define GBLBM_RPT_F16 (4 / GBLBM_COLS_F16)
+#endif
 __host__ __device__ constexpr int direct_rpt(int storage)
 {
-    return storage == LBM_F64 ? 1 : (storage == LBM_F16_DEV ? 4 / GBLBM_COLS_F16 : 2);
+    return storage == LBM_F64 ? 1 : (storage == LBM_F16_DEV ? GBLBM_RPT_F16 : 2);
 }
 
 // ---- D2Q9 (Section II, Table tabD2Q9) as compile-time functions ----
