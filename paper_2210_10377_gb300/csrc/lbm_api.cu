@@ -51,6 +51,7 @@ struct lbm_ctx {
     alignas(64) CUtensorMap tmap[NBUF];                  // [9][ny][pitch] views for TMA loads
     bool tmap_ok = false;
     int use_bulk = 0, sm_count = 1;
+    int pf_tiles = 0;                                    // L2 prefetch distance of the direct kernel
     int cur = 0;                 // buffer holding the latest state
     cudaStream_t side = nullptr; // link kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_read[NBUF] = {nullptr, nullptr, nullptr};
@@ -208,6 +209,7 @@ StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
     memcpy(a.cvt, h->cvt, sizeof(a.cvt));
     a.use_bulk = h->use_bulk;
     a.sm_count = h->sm_count;
+    a.pf_tiles = h->pf_tiles;
     return a;
 }
 
@@ -472,6 +474,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
             h->sm_count = sms;
         else
             cudaGetLastError();
+        h->pf_tiles = collide_stream_prefetch_tiles(bc.storage, h->sm_count);
     }
     h->alloc_fn = bc.alloc;
     h->free_fn = bc.free;
@@ -534,6 +537,9 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     for (int b = 0; b < NBUF; ++b) {
         ALLOC(h->pop_base[b], void *, guard_front + pop_bytes + guard_back);
         h->pop[b] = (char *)h->pop_base[b] + guard_front;
+        // bulk copies and prefetches of rows start on 16-byte boundaries
+        if ((uintptr_t)h->pop_base[b] & 15)
+            return fail(set_err(h, LBM_EINVAL, "the allocator returned a pointer that is not 16-byte aligned"));
     }
     if (h->use_bulk) {
         h->tmap_ok = true;

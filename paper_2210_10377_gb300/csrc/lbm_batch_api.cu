@@ -501,6 +501,8 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
     for (int c = 0; c < 2; ++c) {
         BALLOC(b->pop_base[c], void *, guard_front + pop_bytes + guard_back);
         b->pop[c] = (char *)b->pop_base[c] + guard_front;
+        if ((uintptr_t)b->pop_base[c] & 15)
+            return fail(berr(b, LBM_EINVAL, "the allocator returned a pointer that is not 16-byte aligned"));
         BCKC(cudaMemsetAsync(b->pop_base[c], 0, guard_front + pop_bytes + guard_back, b->stream), "memset");
     }
     BALLOC(b->mask_d, uint8_t *, mask_bytes);

@@ -10,6 +10,13 @@
 
 namespace gblbm {
 
+// Asks L2 for `bytes` bytes of global memory from p (a bulk prefetch through
+// the copy engine; p and bytes multiples of 16).  It changes no value.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes));
+}
+
 // ---------------------------------------------------------------------------
 // Per-node pieces shared by the two collide-stream kernels.
 // ---------------------------------------------------------------------------

@@ -138,6 +138,7 @@ struct StepArgs {
     int cvt[4];              // inclusive tile rectangle holding the box and its halo
     int use_bulk;            // staged (TMA) kernel allowed (channel set-up, pulled state)
     int sm_count;            // persistent grid size of the staged kernel
+    int pf_tiles;            // L2 prefetch distance of the direct kernel in CTAs (0: off)
 };
 
 // The relaxation constants of a StepArgs, from omega: the FP64 set in FP64
@@ -222,6 +223,9 @@ cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
                                   bool momentum_only, const void *tmap, cudaStream_t st);
 size_t tma_stage_bytes(int storage);
+// L2 prefetch distance (StepArgs::pf_tiles) of the direct kernel for a storage
+// type on a device with sm_count SMs; 0 where prefetching is off.
+int collide_stream_prefetch_tiles(int storage, int sm_count);
 cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st);
 cudaError_t launch_gather(int storage, const void *pop, const uint16_t *nbits, const void *inlet,
                           long long plane, int nx, int ny, int pitch, int periodic,

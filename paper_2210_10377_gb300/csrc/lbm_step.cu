@@ -39,6 +39,37 @@ template <> struct DirectMinBlocks<LBM_F16_DEV> {
     static constexpr int value = GBLBM_DIRECT_MINB_F16;
 };
 
+// L2 prefetch distance of the direct kernel, in percent of the CTAs that the
+// GPU holds at once (0: off); a tuning knob.
+#ifndef GBLBM_PF_PERCENT
+#define GBLBM_PF_PERCENT 50
+#endif
+
+// Asks L2 for the source rows of the tile a.pf_tiles CTAs further on in the
+// launch's dispatch order (blockIdx.x fastest): one bulk prefetch per plane and
+// row of that tile, issued by the first 9 TR threads.  The CTA that runs that
+// tile later finds its lines in L2, so HBM requests no longer wait for a
+// warp's load phase.  Each copy lies inside the source buffer (row < ny,
+// columns x0 .. min(x0 + 128, pitch) - 1) and starts on a 16-byte boundary
+// (pitch is a multiple of 64 elements); the halo rows and columns are the
+// neighbouring tiles' own rows.  A prefetch changes no value.
+template <int S>
+__device__ __forceinline__ void prefetch_ahead(const StepArgs &a)
+{
+    using E = typename Traits<S>::store_t;
+    constexpr int TR = tile_rows(S);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + a.pf_tiles;
+    if (a.pf_tiles <= 0 || t >= 9 * TR || lin >= (long long)gridDim.x * gridDim.y) return;
+    const int tx = (int)(lin % gridDim.x) + a.tile_off_x, ty = (int)(lin / gridDim.x) + a.tile_off_y;
+    const int y = ty * TR + t % TR;
+    if (y >= a.ny) return;
+    const int x0 = tx * TILE_X;
+    const int ncol = min(TILE_X, a.pitch - x0);
+    prefetch_l2((const E *)a.src + (long long)(t / TR) * a.plane + (long long)y * a.pitch + x0,
+                (unsigned)(ncol * sizeof(E)));
+}
+
 // Direct-load collide-stream kernel: one CTA of 128 x (TR/RPT) threads per
 // 128 x TR tile; tiles without solids away from the domain's edges take the
 // interior path (collide_tile).
@@ -47,6 +78,7 @@ __global__ void __launch_bounds__((TILE_X / cols_per_thread(S)) * (tile_rows(S) 
                                   DirectMinBlocks<S>::value)
     k_collide_stream(StepArgs a)
 {
+    if constexpr (!MOMENTUM_ONLY) prefetch_ahead<S>(a);
     const int tx = blockIdx.x + a.tile_off_x, ty = blockIdx.y + a.tile_off_y;
     const bool checked = a.precollision || a.tile_flag[(long long)ty * a.tiles_x + tx] != 0;
     collide_tile<S, MOMENTUM_ONLY, FORCE, TILE_X, tile_rows(S), direct_rpt(S)>(a, tx, ty, checked);
@@ -327,6 +359,30 @@ size_t tma_stage_bytes(int storage)
     case LBM_F32_DEV: return TmaCfg<LBM_F32_DEV>::STAGE_BYTES;
     default: return TmaCfg<LBM_F16_DEV>::STAGE_BYTES;
     }
+}
+
+int collide_stream_prefetch_tiles(int storage, int sm_count)
+{
+    if (GBLBM_PF_PERCENT <= 0 || storage == LBM_F64 || sm_count <= 0) return 0;
+    const int threads = (TILE_X / cols_per_thread(storage)) * (tile_rows(storage) / direct_rpt(storage));
+    int per_sm = 0;
+    cudaError_t e;
+    switch (storage) {
+    case LBM_F32:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_stream<LBM_F32, false, false>, threads, 0);
+        break;
+    case LBM_F32_DEV:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_stream<LBM_F32_DEV, false, false>, threads, 0);
+        break;
+    default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_stream<LBM_F16_DEV, false, false>, threads, 0);
+        break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int)((long long)per_sm * sm_count * GBLBM_PF_PERCENT / 100);
 }
 
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,

@@ -402,6 +402,51 @@ def test_allocation_failure_is_reported_and_cleaned_up(gb):
     lat.step(3)
 
 
+def test_misaligned_allocator_pointer_is_refused(gb):
+    # an allocator hook that breaks the 16-byte promise of lbm_bc: creation
+    # fails with EINVAL before any kernel touches the memory, and everything
+    # handed out is given back
+    import ctypes as C
+    import torch
+    L = gb.lib()
+    m = naca(inputs.SMALL_F64)
+    u = np.array([0.05])
+    for batch in (False, True):
+        live = {}
+
+        def alloc(nbytes, stream, user):
+            p = torch.cuda.caching_allocator_alloc(int(nbytes) + 16, 0, stream or 0)
+            live[p + 8] = p
+            return p + 8
+
+        def free(ptr, user):
+            torch.cuda.caching_allocator_delete(live.pop(ptr))
+
+        fa, ff = gb.ALLOC_FN(alloc), gb.FREE_FN(free)
+        bc = gb.lbm_bc()
+        L.lbm_bc_default(C.byref(bc))
+        bc.storage = gb.F16_DEV
+        bc.alloc, bc.free = fa, ff
+        h = C.c_void_p()
+        if batch:
+            dom = (gb.lbm_domain * 1)()
+            dom[0].mask = m.ctypes.data_as(C.POINTER(C.c_uint8))
+            dom[0].ny, dom[0].nx = m.shape
+            dom[0].tau, dom[0].u_in, dom[0].n_u_in = 0.6, gb._dp(u), 1
+            for j in range(4):
+                dom[0].cv[j] = -1
+            rc = L.lbm_batch_create(dom, 1, C.byref(bc), C.byref(h))
+            assert b"16-byte" in L.lbm_batch_last_error(None)
+        else:
+            rc = L.lbm_create(m.ctypes.data_as(C.POINTER(C.c_uint8)), m.shape[1], m.shape[0], 0.6,
+                              gb._dp(u), 1, C.byref(bc), C.byref(h))
+            assert b"16-byte" in L.lbm_last_error(None)
+        assert rc == 1 and not h.value, (batch, rc)
+        assert live == {}
+    lat = gb.Lattice(m, 0.6, 0.05, storage="f16dev")
+    lat.step(3)
+
+
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f16dev", 1e-3)])
 def test_force_series_2000_steps_scaled_bench_geometry(gb, storage, tol):
     # the bench geometry shrunk 8x (512 x 256, chord 32 at 4 deg, same tau): every
