@@ -364,6 +364,29 @@ def test_staged_kernel_matches_direct_kernel(gb, storage):
                 assert np.abs(a.force_series(s)[k] - b.force_series(s)[k]).max() <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16dev"])
+def test_l2_prefetch_on_a_large_ragged_grid(gb, storage):
+    # The direct kernel prefetches into L2 the rows of the tile half the
+    # resident CTAs ahead, so only grids of thousands of tiles exercise it.
+    # On a grid whose last tile column (64 of 128 columns in the pitch) and
+    # last tile row (2 of 4 or 8 rows) are ragged, the prefetching direct kernel
+    # equals the staged kernel, which does not prefetch, bit for bit.
+    nx, ny = 4160, 2050
+    mask = gb.naca_mask(nx, ny, 260.0, 0.12, 4.0, 1300.0, (ny - 1) / 2.0)
+    runs = []
+    for kernel in ("staged", "direct"):
+        lat = gb.Lattice(mask, 0.5384, 0.05, storage=storage, kernel=kernel)
+        lat.step(1)
+        lat.step(20)
+        runs.append(lat)
+    a, b = runs
+    assert np.array_equal(a.populations(), b.populations())
+    for s in ("A", "B", "A_RTT", "SI"):
+        assert np.array_equal(a.force_series(s)[0], b.force_series(s)[0]), s
+    for lat in runs:
+        lat.close()
+
+
 def test_allocation_failure_is_reported_and_cleaned_up(gb):
     # fault injection on the host: an allocator hook that refuses the k-th request
     import ctypes as C
