@@ -51,7 +51,7 @@ struct lbm_ctx {
     alignas(64) CUtensorMap tmap[NBUF];                  // [9][ny][pitch] views for TMA loads
     bool tmap_ok = false;
     int use_bulk = 0, sm_count = 1;
-    int pf_tiles = 0;                                    // L2 prefetch distance of the direct kernel
+    int pf_rows = 0;                                     // L2 prefetch distance of the direct kernel
     int cur = 0;                 // buffer holding the latest state
     cudaStream_t side = nullptr; // link kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_read[NBUF] = {nullptr, nullptr, nullptr};
@@ -209,7 +209,7 @@ StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
     memcpy(a.cvt, h->cvt, sizeof(a.cvt));
     a.use_bulk = h->use_bulk;
     a.sm_count = h->sm_count;
-    a.pf_tiles = h->pf_tiles;
+    a.pf_rows = h->pf_rows;
     return a;
 }
 
@@ -474,7 +474,6 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
             h->sm_count = sms;
         else
             cudaGetLastError();
-        h->pf_tiles = collide_stream_prefetch_tiles(bc.storage, h->sm_count);
     }
     h->alloc_fn = bc.alloc;
     h->free_fn = bc.free;
@@ -483,6 +482,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     h->pitch = (nx + PITCH_ALIGN - 1) / PITCH_ALIGN * PITCH_ALIGN;
     h->plane = (long long)ny * h->pitch;
     h->tiles_x = (nx + TILE_X - 1) / TILE_X;
+    h->pf_rows = collide_stream_prefetch_rows(bc.storage, h->sm_count, h->tiles_x);
     h->tiles_y = (ny + tile_rows(h->storage) - 1) / tile_rows(h->storage);
     cv_tile_rect(cv, nx, ny, TILE_X, tile_rows(h->storage), h->cvt);
     h->n_cv_tiles = (h->cvt[1] - h->cvt[0] + 1) * (h->cvt[3] - h->cvt[2] + 1);

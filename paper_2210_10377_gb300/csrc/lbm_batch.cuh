@@ -26,15 +26,18 @@ namespace gblbm {
 #endif
 constexpr int BATCH_SHAPES = 3;
 __host__ __device__ constexpr int batch_tx(int shape) { return shape == 0 ? 128 : (shape == 1 ? 64 : 32); }
-// FP16 deviations: 8-row tiles at 128 wide (1024 nodes, as FP32), so the
-// per-tile domain look-up is spread over as many nodes
+// Rows of the 128-wide shape: 8 for FP32 and FP16 deviations (1024 nodes, so
+// that the per-tile domain look-up is spread over as many nodes), 4 for FP64
 #ifndef GBLBM_BATCH_ROWS_F16
 #define GBLBM_BATCH_ROWS_F16 8
 #endif
+#ifndef GBLBM_BATCH_ROWS_F32
+#define GBLBM_BATCH_ROWS_F32 8
+#endif
 __host__ __device__ constexpr int batch_tr(int storage, int shape)
 {
-    return (storage == LBM_F16_DEV ? GBLBM_BATCH_ROWS_F16 : tile_rows(storage)) * (128 / batch_tx(shape)) /
-           ((storage == LBM_F32 || storage == LBM_F32_DEV) ? GBLBM_BATCH_TRDIV : 1);
+    return (storage == LBM_F16_DEV ? GBLBM_BATCH_ROWS_F16 : (storage == LBM_F64 ? 4 : GBLBM_BATCH_ROWS_F32)) *
+           (128 / batch_tx(shape)) / ((storage == LBM_F32 || storage == LBM_F32_DEV) ? GBLBM_BATCH_TRDIV : 1);
 }
 __host__ __device__ constexpr int batch_rpt(int storage)
 {

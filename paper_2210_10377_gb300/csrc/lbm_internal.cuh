@@ -40,13 +40,16 @@ constexpr int CV_PARTIAL = 6;
 constexpr int LINK_PARTIAL = 14;
 constexpr int SERIES_ROW = 12;
 
-// Tile rows of the FP16-deviation kernels (a tuning knob).
+// Tile rows of the FP32 and FP16-deviation kernels (tuning knobs).
 #ifndef GBLBM_TR_F16
 #define GBLBM_TR_F16 4
 #endif
+#ifndef GBLBM_TR_F32
+#define GBLBM_TR_F32 4
+#endif
 __host__ __device__ constexpr int tile_rows(int storage)
 {
-    return (storage == LBM_F32 || storage == LBM_F32_DEV) ? 8 : (storage == LBM_F16_DEV ? GBLBM_TR_F16 : 4);
+    return (storage == LBM_F32 || storage == LBM_F32_DEV) ? GBLBM_TR_F32 : (storage == LBM_F16_DEV ? GBLBM_TR_F16 : 4);
 }
 // Adjacent columns per thread of the direct-load kernels: FP16 deviations
 // take two, so that loads and stores move 4-byte pairs (a tuning knob).
@@ -138,7 +141,7 @@ struct StepArgs {
     int cvt[4];              // inclusive tile rectangle holding the box and its halo
     int use_bulk;            // staged (TMA) kernel allowed (channel set-up, pulled state)
     int sm_count;            // persistent grid size of the staged kernel
-    int pf_tiles;            // L2 prefetch distance of the direct kernel in CTAs (0: off)
+    int pf_rows;             // L2 prefetch distance of the direct kernel in tile rows (0: off)
 };
 
 // The relaxation constants of a StepArgs, from omega: the FP64 set in FP64
@@ -223,9 +226,10 @@ cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
                                   bool momentum_only, const void *tmap, cudaStream_t st);
 size_t tma_stage_bytes(int storage);
-// L2 prefetch distance (StepArgs::pf_tiles) of the direct kernel for a storage
-// type on a device with sm_count SMs; 0 where prefetching is off.
-int collide_stream_prefetch_tiles(int storage, int sm_count);
+// L2 prefetch distance (StepArgs::pf_rows) of the direct kernel for a storage
+// type on a device with sm_count SMs and tiles_x tiles per row; 0 where
+// prefetching is off.
+int collide_stream_prefetch_rows(int storage, int sm_count, int tiles_x);
 cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st);
 cudaError_t launch_gather(int storage, const void *pop, const uint16_t *nbits, const void *inlet,
                           long long plane, int nx, int ny, int pitch, int periodic,

@@ -18,13 +18,14 @@
 namespace gblbm {
 
 // Minimum resident CTAs per SM asked of the compiler for the direct kernel
-// (0: no bound); tuning knobs.  FP16 storage is occupancy-bound: 8 CTAs of 128
-// threads (64 registers) run it faster than fewer CTAs without spills.
+// (0: no bound); tuning knobs.  FP32 and FP16 storage are occupancy-bound:
+// 4 CTAs of 256 threads (FP32) and 8 of 128 (FP16), 64 registers each, run
+// them faster than fewer CTAs without spills.
 #ifndef GBLBM_DIRECT_MINB_F16
 #define GBLBM_DIRECT_MINB_F16 8
 #endif
 #ifndef GBLBM_DIRECT_MINB_F32
-#define GBLBM_DIRECT_MINB_F32 2
+#define GBLBM_DIRECT_MINB_F32 4
 #endif
 template <int S> struct DirectMinBlocks {
     static constexpr int value = 0;
@@ -45,26 +46,26 @@ template <> struct DirectMinBlocks<LBM_F16_DEV> {
 #define GBLBM_PF_PERCENT 50
 #endif
 
-// Asks L2 for the source rows of the tile a.pf_tiles CTAs further on in the
-// launch's dispatch order (blockIdx.x fastest): one bulk prefetch per plane and
-// row of that tile, issued by the first 9 TR threads.  The CTA that runs that
-// tile later finds its lines in L2, so HBM requests no longer wait for a
-// warp's load phase.  Each copy lies inside the source buffer (row < ny,
-// columns x0 .. min(x0 + 128, pitch) - 1) and starts on a 16-byte boundary
-// (pitch is a multiple of 64 elements); the halo rows and columns are the
-// neighbouring tiles' own rows.  A prefetch changes no value.
+// Asks L2 for the source rows of the tile a.pf_rows tile rows further down
+// the same tile column: in the launch's dispatch order (blockIdx.x fastest)
+// that tile runs about pf_rows * tiles_x CTAs later, and its CTA then finds
+// its lines in L2, so HBM requests no longer wait for a warp's load phase.
+// One bulk prefetch per plane and row of that tile, issued by the first 9 TR
+// threads.  Each copy lies inside the source buffer (row < ny, columns x0 ..
+// min(x0 + 128, pitch) - 1) and starts on a 16-byte boundary (pitch is a
+// multiple of 64 elements); the halo rows and columns are the neighbouring
+// tiles' own rows.  A prefetch changes no value.
 template <int S>
 __device__ __forceinline__ void prefetch_ahead(const StepArgs &a)
 {
     using E = typename Traits<S>::store_t;
     constexpr int TR = tile_rows(S);
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + a.pf_tiles;
-    if (a.pf_tiles <= 0 || t >= 9 * TR || lin >= (long long)gridDim.x * gridDim.y) return;
-    const int tx = (int)(lin % gridDim.x) + a.tile_off_x, ty = (int)(lin / gridDim.x) + a.tile_off_y;
+    const int ty = (int)blockIdx.y + a.pf_rows;
+    if (a.pf_rows <= 0 || t >= 9 * TR || ty >= (int)gridDim.y) return;
     const int y = ty * TR + t % TR;
     if (y >= a.ny) return;
-    const int x0 = tx * TILE_X;
+    const int x0 = (int)blockIdx.x * TILE_X;
     const int ncol = min(TILE_X, a.pitch - x0);
     prefetch_l2((const E *)a.src + (long long)(t / TR) * a.plane + (long long)y * a.pitch + x0,
                 (unsigned)(ncol * sizeof(E)));
@@ -361,9 +362,9 @@ size_t tma_stage_bytes(int storage)
     }
 }
 
-int collide_stream_prefetch_tiles(int storage, int sm_count)
+int collide_stream_prefetch_rows(int storage, int sm_count, int tiles_x)
 {
-    if (GBLBM_PF_PERCENT <= 0 || storage == LBM_F64 || sm_count <= 0) return 0;
+    if (GBLBM_PF_PERCENT <= 0 || storage == LBM_F64 || sm_count <= 0 || tiles_x <= 0) return 0;
     const int threads = (TILE_X / cols_per_thread(storage)) * (tile_rows(storage) / direct_rpt(storage));
     int per_sm = 0;
     cudaError_t e;
@@ -382,7 +383,9 @@ int collide_stream_prefetch_tiles(int storage, int sm_count)
         cudaGetLastError();
         return 0;
     }
-    return (int)((long long)per_sm * sm_count * GBLBM_PF_PERCENT / 100);
+    const long long tiles = (long long)per_sm * sm_count * GBLBM_PF_PERCENT / 100;
+    const long long rows = (tiles + tiles_x / 2) / tiles_x;
+    return (int)(rows < 1 ? 1 : rows);
 }
 
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
