@@ -512,8 +512,9 @@ __device__ __forceinline__ void column_pair_update_interior(const StepArgs &a, i
 // One tile of TX x TR nodes with (TX/COLS) x (TR/RPT) threads (threadIdx.x:
 // COLS adjacent columns, threadIdx.y: group of RPT rows).  `checked` selects the bounce-back-aware
 // path (solid nodes in or next to the tile, or a pre-collision state).  A
-// block that met rho <= 0 or NaN sets status bit 0 and the first bad step.
-// All threads of the block must call it (it synchronises).
+// warp that met rho <= 0 or NaN sets status bit 0 and the first bad step.
+// All threads of the block must call it: control-volume tiles synchronise the
+// block, and the vote needs every lane of a warp.
 // ---------------------------------------------------------------------------
 template <int S, bool MOMENTUM_ONLY, bool FORCE, int TX, int TR, int RPT>
 __device__ __forceinline__ void collide_tile(const StepArgs &a, int tx, int ty, bool checked)
@@ -553,8 +554,10 @@ __device__ __forceinline__ void collide_tile(const StepArgs &a, int tx, int ty, 
     }
     if (cvtile) cv_store<S, MOMENTUM_ONLY, (TX / COLS) * (TR / RPT)>(a, tx, ty, acc);
     if (!MOMENTUM_ONLY) {
-        const int any_bad = __syncthreads_or(bad);
-        if (any_bad && threadIdx.x == 0 && threadIdx.y == 0) {
+        // one vote per warp rather than per block: no barrier, so a warp that
+        // is done leaves at once (the flags are idempotent: OR and MIN)
+        const unsigned any_bad = __ballot_sync(0xffffffffu, bad);
+        if (any_bad && ((threadIdx.y * blockDim.x + threadIdx.x) & 31) == 0) {
             atomicOr(a.status, 1);
             atomicMin(a.status + 1, (int)*a.step_ctr);
         }

@@ -35,6 +35,12 @@ constexpr int TILE_X = 128;
 constexpr unsigned int WAIT_LIMIT = 1u << 22;  // bound on every mbarrier wait loop
 constexpr int PITCH_ALIGN = 64;
 constexpr int LINK_THREADS = 128;
+// Threads of the batched link kernel's one CTA per domain (a tuning knob):
+// enough that a domain's links take one pass.
+#ifndef GBLBM_BATCH_LINK_THREADS
+#define GBLBM_BATCH_LINK_THREADS 512
+#endif
+constexpr int BATCH_LINK_THREADS = GBLBM_BATCH_LINK_THREADS;
 constexpr int MAX_LINK_CTAS = 148;
 constexpr int CV_PARTIAL = 6;
 constexpr int LINK_PARTIAL = 14;

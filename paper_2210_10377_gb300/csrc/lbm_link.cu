@@ -31,7 +31,10 @@ namespace gblbm {
 // pairs along each axis, so the constant rho0/3 sums to zero, and leaving it
 // out keeps the FP32 sums free of its cancellation.
 // ---------------------------------------------------------------------------
-template <int S>
+// NT threads share the ranges.  EARLY: a thread's first partial row is loaded
+// before the link loop, so that its latency overlaps the links' (the sums keep
+// their order).
+template <int S, int NT, bool EARLY>
 __device__ __forceinline__ void link_sums(const LinkArgs &a, long long k0, long long k1, int p0, int p1,
                                           typename AccOf<S>::type (&v)[LINK_PARTIAL])
 {
@@ -43,7 +46,17 @@ __device__ __forceinline__ void link_sums(const LinkArgs &a, long long k0, long 
     const long long plane = a.plane;
 #pragma unroll
     for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(v[k]);
-    for (long long k = k0 + threadIdx.x; k < k1; k += LINK_THREADS) {
+    const A *part = (const A *)a.partials;
+    const int s0 = p0 + (int)threadIdx.x;
+    A first[CV_PARTIAL];
+#pragma unroll
+    for (int k = 0; k < CV_PARTIAL; ++k) {
+        if (EARLY && s0 < p1)
+            first[k] = part[CV_PARTIAL * (long long)s0 + k];
+        else
+            acc_zero(first[k]);
+    }
+    for (long long k = k0 + threadIdx.x; k < k1; k += NT) {
         const int l = a.links[k];
         const int n = l >> 3;
         const int i = (l & 7) + 1;
@@ -133,8 +146,11 @@ __device__ __forceinline__ void link_sums(const LinkArgs &a, long long k0, long 
             acc_add(v[5], ey > 0 ? sp : -sp);
         }
     }
-    const A *part = (const A *)a.partials;
-    for (int s = p0 + threadIdx.x; s < p1; s += LINK_THREADS) {
+    if (EARLY && s0 < p1) {
+#pragma unroll
+        for (int k = 0; k < CV_PARTIAL; ++k) acc_add(v[6 + k], first[k]);
+    }
+    for (int s = EARLY ? s0 + NT : s0; s < p1; s += NT) {
 #pragma unroll
         for (int k = 0; k < CV_PARTIAL; ++k) acc_add(v[6 + k], part[CV_PARTIAL * (long long)s + k]);
     }
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
         const int per_p = (a.n_partials + gridDim.x - 1) / gridDim.x;
         const int p0 = per_p * blockIdx.x;
         const int p1 = p0 + per_p < a.n_partials ? p0 + per_p : a.n_partials;
-        link_sums<S>(a, k0, k1 > k0 ? k1 : k0, p0, p1 > p0 ? p1 : p0, v);
+        link_sums<S, LINK_THREADS, false>(a, k0, k1 > k0 ? k1 : k0, p0, p1 > p0 ? p1 : p0, v);
     }
     block_reduce<A, LINK_PARTIAL, LINK_THREADS>(v);
     __shared__ bool last;
@@ -280,7 +296,7 @@ cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st)
 // advances the counter, so no CTA can see the new value.
 // ---------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(LINK_THREADS) k_link_force_batch(BatchLinkArgs b)
+__global__ void __launch_bounds__(BATCH_LINK_THREADS) k_link_force_batch(BatchLinkArgs b)
 {
     using A = typename AccOf<S>::type;
     static_assert(sizeof(LinkArgs) % 4 == 0, "LinkArgs is copied as 32-bit words");
@@ -290,13 +306,13 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force_batch(BatchLinkArgs
     {
         const int *src = (const int *)(b.args + blockIdx.x);
         int *dst = (int *)&la;
-        for (int w = threadIdx.x; w < WORDS; w += LINK_THREADS) dst[w] = src[w];
+        for (int w = threadIdx.x; w < WORDS; w += BATCH_LINK_THREADS) dst[w] = src[w];
         if (threadIdx.x == 0) t_sh = *(volatile long long *)b.step_ctr;
     }
     __syncthreads();
     A v[LINK_PARTIAL];
-    link_sums<S>(la, 0, b.drtt_only ? 0 : la.nlinks, 0, la.n_partials, v);
-    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(v);
+    link_sums<S, BATCH_LINK_THREADS, true>(la, 0, b.drtt_only ? 0 : la.nlinks, 0, la.n_partials, v);
+    block_reduce<A, LINK_PARTIAL, BATCH_LINK_THREADS>(v);
     if (threadIdx.x == 0) {
         double d[LINK_PARTIAL];
 #pragma unroll
@@ -332,10 +348,10 @@ cudaError_t launch_link_force_batch(int storage, const BatchLinkArgs &b, cudaStr
     const int grid = b.n_domains;
     if (grid < 1) return cudaSuccess;
     switch (storage) {
-    case LBM_F64: k_link_force_batch<LBM_F64><<<grid, LINK_THREADS, 0, st>>>(b); break;
-    case LBM_F32: k_link_force_batch<LBM_F32><<<grid, LINK_THREADS, 0, st>>>(b); break;
-    case LBM_F32_DEV: k_link_force_batch<LBM_F32_DEV><<<grid, LINK_THREADS, 0, st>>>(b); break;
-    default: k_link_force_batch<LBM_F16_DEV><<<grid, LINK_THREADS, 0, st>>>(b); break;
+    case LBM_F64: k_link_force_batch<LBM_F64><<<grid, BATCH_LINK_THREADS, 0, st>>>(b); break;
+    case LBM_F32: k_link_force_batch<LBM_F32><<<grid, BATCH_LINK_THREADS, 0, st>>>(b); break;
+    case LBM_F32_DEV: k_link_force_batch<LBM_F32_DEV><<<grid, BATCH_LINK_THREADS, 0, st>>>(b); break;
+    default: k_link_force_batch<LBM_F16_DEV><<<grid, BATCH_LINK_THREADS, 0, st>>>(b); break;
     }
     return cudaGetLastError();
 }
