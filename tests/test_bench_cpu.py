@@ -29,6 +29,8 @@ def test_reference_arm_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"].startswith("naca0012_4096x2048")
+    # the contract's K and W: K timed steps after W warm-up steps, each a bounded sample
+    assert d["steps"] == 2 and d["warmup"] == 0 and "band" in d["cpu_baseline"]["sample"]
 
 
 def test_reference_arm_two_ranks_only_rank0_prints():
