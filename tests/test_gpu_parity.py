@@ -512,3 +512,36 @@ def test_pressure_coefficient_matches_oracle(gb, storage):
             on, oc = sim.surface_pressure(p_inf, q)
             assert np.array_equal(on, gn) and np.abs(gc - oc).max() <= 1e-10, n
     lat.close()
+
+
+def _golden_rows(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                yield line.split()
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-15), ("f32", 2e-7), ("f16dev", 2e-4)])
+def test_step0_forces_match_hand_derived_golden(gb, storage, tol):
+    # the CUDA path against the hand-derived closed forms of tests/golden/step0_forces.txt
+    # (link counts per direction, algorithms A, B and A' at t = 0 in a uniform equilibrium)
+    from fractions import Fraction
+    for row in _golden_rows("step0_forces.txt"):
+        name, nx, ny, cells = row[0], int(row[1]), int(row[2]), row[3]
+        counts = [int(v) for v in row[4:12]]
+        bx, by, ax, ay = (float(Fraction(v)) for v in row[12:16])
+        m = np.zeros((ny, nx), np.uint8)
+        for c in cells.split(";"):
+            x, y = (int(v) for v in c.split(","))
+            m[y, x] = 1
+        lat = gb.Lattice(m, 0.7, 0.05, kind=gb.PERIODIC, storage=storage)
+        links = lat.links()
+        assert np.bincount(links % 8 + 1, minlength=9)[1:].tolist() == counts, name
+        lat.step(1)
+        for scheme, want in (("B", (bx, by)), ("A", (ax, ay)), ("A_RTT", (bx, by))):
+            got = lat.force(scheme)
+            assert abs(got[0] - want[0]) <= tol and abs(got[1] - want[1]) <= tol, (name, storage, scheme, got)
+        lat.close()
