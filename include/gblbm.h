@@ -96,8 +96,10 @@ typedef enum {
 } lbm_scheme;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
- * alloc returns a device pointer (16-byte aligned at least) or NULL; stream is
- * the handle's stream.  free releases a pointer from alloc. */
+ * alloc returns a device pointer (16-byte aligned at least: the kernels'
+ * bulk copies and L2 prefetches start on 16-byte boundaries, and creation
+ * fails with EINVAL on a pointer that is not) or NULL; stream is the handle's
+ * stream.  free releases a pointer from alloc. */
 typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*lbm_free_fn)(void *ptr, void *user);
 
@@ -138,7 +140,8 @@ void lbm_bc_default(lbm_bc *bc);
  * EINVAL: nx < 4, ny < 3, 8*nx*ny >= 2^31, tau <= 0.5, non-finite input, bad
  * kind/storage/n_u_in, rho0 <= 0, a solid node in columns 0, 1, nx-2, nx-1 of a
  * channel, or a control volume that touches the inlet/outlet column or
- * straddles a periodic edge (it must lie within [1, n-2] or span [0, n-1]).
+ * straddles a periodic edge (it must lie within [1, n-2] or span [0, n-1]),
+ * or a population buffer from bc->alloc that is not 16-byte aligned.
  * ENOMEM / ECUDA as named.  On success *out receives the handle. */
 lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const double *u_in,
                       int n_u_in, const lbm_bc *bc, lbm_ctx **out);
@@ -322,7 +325,8 @@ typedef struct {
  * configuration starts at tile shape 0 with one CTA per tile;
  * lbm_batch_autotune picks a faster one.
  * EINVAL: n < 1, any domain failing lbm_create's checks (the message names
- * the domain), a nonzero body force, bc->kernel != 0.  ENOMEM / ECUDA as named. */
+ * the domain), a nonzero body force, bc->kernel != 0, a population arena from
+ * bc->alloc that is not 16-byte aligned.  ENOMEM / ECUDA as named. */
 lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc, lbm_batch **out);
 
 /* Advance every domain n >= 0 steps (as lbm_step, for each domain).
