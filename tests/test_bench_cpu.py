@@ -70,3 +70,19 @@ def test_reduce_max_single_process_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.reduce_max(3.5) == 3.5
+
+
+def test_reference_arm_band_sample():
+    # the reference arm's bounded sample: a thin band takes the all-fluid top
+    # rows; a band of at least half the height is centred and holds the airfoil
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2210_10377_gb300 import inputs
+    w = inputs.LARGE_F32
+    thin, y0 = bench.oracle_band(w, 3)
+    assert thin.shape == (3, w.nx) and y0 == w.ny - 3 and thin.sum() == 0
+    thick, y0 = bench.oracle_band(w, w.ny // 2)
+    assert thick.shape == (w.ny // 2, w.nx) and y0 == w.ny // 4
+    import oracle
+    full = oracle.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
+    assert thick.sum() == full.sum() > 0
