@@ -545,3 +545,36 @@ def test_step0_forces_match_hand_derived_golden(gb, storage, tol):
             got = lat.force(scheme)
             assert abs(got[0] - want[0]) <= tol and abs(got[1] - want[1]) <= tol, (name, storage, scheme, got)
         lat.close()
+
+
+PREFIX_CASES = [
+    ("naca0012_4096x2048_c256_a4_re1000_f32", "naca0012_4096x2048_c256_a4_re1000_oracle_prefix5000.txt",
+     "f32", 1e-4),
+    ("naca0012_8192x4096_c512_a6_re2000_f16dev", "naca0012_8192x4096_c512_a6_re2000_oracle_prefix1000.txt",
+     "f32dev", 1e-4),
+    ("naca0012_8192x4096_c512_a6_re2000_f16dev", "naca0012_8192x4096_c512_a6_re2000_oracle_prefix1000.txt",
+     "f16dev", 1e-3),
+]
+
+
+@pytest.mark.parametrize("name,fixture,storage,tol", PREFIX_CASES,
+                         ids=["4096x2048-f32-5000", "8192x4096-f32dev-1000", "8192x4096-f16dev-1000"])
+def test_full_size_force_series_against_stored_oracle(gb, name, fixture, storage, tol):
+    # The full-size workloads' per-step drag and lift of every scheme against the
+    # FP64 oracle's series over their first steps, stored by
+    # tests/golden/make_prefix_series.py (every 10th / 5th step), on the scale of
+    # the largest force of the window (FP32 1e-4, FP16 deviations 1e-3).
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", fixture))
+    t = rows[:, 0].astype(int)
+    w = inputs.WORKLOADS[name]
+    lat = gb.Lattice(gb.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc),
+                     w.tau, w.u_in, storage=storage)
+    lat.step(int(t[-1]) + 2)  # DRTT of the last stored step needs the next one
+    scale = np.abs(rows[:, 1:]).max()
+    for j, s in enumerate(("A", "B", "DRTT", "A_RTT", "SI")):
+        gx, gy = lat.force_series(s)
+        ex = np.abs(gx[t] - rows[:, 1 + 2 * j]).max()
+        ey = np.abs(gy[t] - rows[:, 2 + 2 * j]).max()
+        assert ex <= tol * scale and ey <= tol * scale, (s, ex / scale, ey / scale)
+    lat.close()
