@@ -70,3 +70,27 @@ def test_stored_prefix_series_obey_the_paper(name, fixture):
     # the file stores 13 significant digits (5e-13 relative)
     assert abs(bx[0] - 2 * (n * cx * feq).sum()) <= 1e-12 * scale
     assert abs(by[0] - 2 * (n * cy * feq).sum()) <= 1e-12 * scale
+
+
+def test_prefix_series_generator_writes_the_oracle_series(tmp_path):
+    # the generator of the stored series, run on the small differentiation
+    # workload: its rows are the oracle's own series at the stored steps
+    import subprocess
+    import sys
+    from paper_2210_10377_gb300 import inputs
+    name = inputs.DIFF.name
+    out = tmp_path / "series.txt"
+    script = os.path.join(GOLDEN, "make_prefix_series.py")
+    r = subprocess.run([sys.executable, script, name, "12", "4", str(out)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    rows = np.loadtxt(out)
+    assert rows[:, 0].tolist() == [0, 4, 8]
+    w = inputs.DIFF
+    sim = oracle.Sim(oracle.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc), w.tau, w.u_in)
+    sim.step(13)
+    for j, k in enumerate((oracle.SCHEME_A, oracle.SCHEME_B, oracle.SCHEME_DRTT, oracle.SCHEME_A_RTT,
+                           oracle.SCHEME_SI)):
+        fx, fy = sim.force_series(k, 0, 12)
+        np.testing.assert_allclose(rows[:, 1 + 2 * j], fx[[0, 4, 8]], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(rows[:, 2 + 2 * j], fy[[0, 4, 8]], rtol=1e-12, atol=1e-14)
