@@ -3,6 +3,9 @@ steps (a golden fixture for the GPU parity tests).  It runs only the oracle.
 
     python tests/golden/make_prefix_series.py WORKLOAD STEPS STRIDE OUT
 
+WORKLOAD is a named workload, or one with the suffix _divK: the same geometry
+shrunk K times (inputs.scaled).
+
 Every STRIDE-th step t = 0, STRIDE, ... < STEPS gets one row: t, then F_x and
 F_y of algorithm A (Eq. MEA on the pre-collision state), algorithm B (Eq.
 rtt5), DRTT (Eq. rtt7), A' (Eq. rtt4) and stress integration (Eq.
@@ -24,7 +27,8 @@ SCHEMES = (("A", oracle.SCHEME_A), ("B", oracle.SCHEME_B), ("DRTT", oracle.SCHEM
 
 def main():
     name, steps, stride, out = sys.argv[1], int(sys.argv[2]), int(sys.argv[3]), sys.argv[4]
-    w = inputs.WORKLOADS[name]
+    base, _, div = name.rpartition("_div")
+    w = inputs.scaled(inputs.WORKLOADS[base], int(div)) if base and div.isdigit() else inputs.WORKLOADS[name]
     m = oracle.naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
     sim = oracle.Sim(m, w.tau, w.u_in)
     t0 = time.time()
