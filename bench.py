@@ -52,6 +52,11 @@ def args_():
                         "NACA00xx recipe instead of one workload")
     p.add_argument("--batch-launch", default=None,
                    help="profile mode: 'shape,ctas_per_sm' for the batch instead of the tuner")
+    p.add_argument("--adjoint", type=int, default=0,
+                   help="profile mode: run lbm_adjoint over this many steps (window: the last half) "
+                        "instead of stepping")
+    p.add_argument("--shrink", type=int, default=1,
+                   help="profile mode: the workload's geometry shrunk by this integer factor")
     return p.parse_args()
 
 
@@ -138,10 +143,27 @@ class Clocks:
                 stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the first sample lands before the timed region starts
+        self._wait_rows(1, 5.0)
+
+    def _rows(self):
+        try:
+            with open(self.file.name) as f:
+                return sum(1 for line in f if line.count(",") >= 8)
+        except Exception:
+            return 0
+
+    def _wait_rows(self, n, limit):
+        t0 = time.time()
+        while self.proc is not None and self.proc.poll() is None and self._rows() < n and time.time() - t0 < limit:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
             return None
+        # at least one sample after the timed region, however short it was
+        self._wait_rows(self._rows() + 1, 2.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -172,14 +194,78 @@ def naca_mask_device(w):
 
 
 def time_steps(torch, lat, steps):
+    """Device time of `steps` steps: CUDA events on the handle's stream around
+    the queued steps (lbm_step_async), then the wait and the status check."""
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(lat.stream)
-    lat.step(steps)
+    lat.step_async(steps)
     e1.record(lat.stream)
+    lat.sync()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+# Stored FP64 oracle force series of the full-size workloads' first steps
+# (written by tests/golden/make_prefix_series.py from the oracle alone):
+# columns t, then F_x F_y of A, B, DRTT, A', SI.
+PREFIX_SERIES = {
+    "naca0012_4096x2048_c256_a4_re1000_f32":
+        "naca0012_4096x2048_c256_a4_re1000_oracle_prefix5000.txt",
+    "naca0012_8192x4096_c512_a6_re2000_f16dev":
+        "naca0012_8192x4096_c512_a6_re2000_oracle_prefix1000.txt",
+}
+COEFF_SCHEMES = ("A", "B", "DRTT", "A_RTT", "SI")
+
+
+def load_prefix(workload):
+    """(t[n], F[5][2][n]) of the stored oracle series of a workload."""
+    rows = np.loadtxt(os.path.join(ROOT, "tests", "golden", PREFIX_SERIES[workload]))
+    t = rows[:, 0].astype(int)
+    return t, rows[:, 1:].reshape(len(t), 5, 2).transpose(1, 2, 0)
+
+
+def coeff_errors(lat, w, t, oracle_f, upto=None):
+    """Drag and lift coefficients of every scheme (the library's
+    lbm_coefficients) against the stored oracle series, at the stored steps
+    below `upto` (default: all steps whose DRTT is complete).  Per step the
+    error is relative to S(t) = max over compared steps s >= min(t, n/2) of
+    max(|C_d(s)|, |C_l(s)|) of the oracle (the back half is judged against its
+    largest coefficient; the force of the impulsive start sets the scale only
+    for itself and its decay); the mean is over the back half of the compared
+    steps, relative to max(|mean C_d|, |mean C_l|)."""
+    upto = lat.steps_done - 1 if upto is None else upto
+    keep = t < upto
+    tk = t[keep]
+    if tk.size < 2:
+        return {"steps_compared": int(tk.size)}
+    norm = 2.0 / (w.rho0 * w.u_in ** 2 * w.chord)
+    out = {"steps_compared": int(tk.size), "last_step": int(tk[-1])}
+    h = tk.size // 2
+    for j, s in enumerate(COEFF_SCHEMES):
+        cd, cl, _ = lat.coefficients(s, w.chord, w.u_in, 0, int(tk[-1]) + 1)
+        g = np.stack([cd[tk], cl[tk]])
+        o = norm * oracle_f[j][:, keep]
+        mag = np.abs(o).max(axis=0)
+        env = np.maximum.accumulate(mag[::-1])[::-1]
+        env[h:] = env[h]
+        per_step = float((np.abs(g - o).max(axis=0) / env).max())
+        mo, mg = o[:, h:].mean(axis=1), g[:, h:].mean(axis=1)
+        out[s] = {"per_step": per_step, "mean": float(np.abs(mg - mo).max() / np.abs(mo).max())}
+    return out
+
+
+def prefix_accuracy(binding, w, storage, device):
+    """A run over the whole stored prefix of a workload: coefficient errors
+    of every scheme (see coeff_errors)."""
+    t, o = load_prefix(w.name)
+    lat = binding.Lattice(naca_mask_device(w), w.tau, w.u_in, storage=storage, device=device)
+    lat.step(int(t[-1]) + 2)
+    out = {"workload": w.name, "storage": storage, "oracle_steps": "0..%d every %d" % (t[-1], t[1] - t[0])}
+    out.update(coeff_errors(lat, w, t, o))
+    lat.close()
+    return out
 
 
 def kernel_roofline(torch, lat, w, storage, steps, peak):
@@ -342,9 +428,12 @@ def run_ours(a):
     storage = w.storage
     peak, peak_kind = measured_peaks()
 
-    # -- device throughput: inputs resident, K steps between barriers
+    # -- device throughput: inputs resident, K steps between barriers.  The
+    # force series is grown and every captured step graph built before the
+    # warm-up (lbm_prepare), so the timed steps only launch.
     mask = naca_mask_device(w)
     lat = binding.Lattice(mask, w.tau, w.u_in, storage=storage, device=local)
+    lat.prepare(a.warmup + a.steps + 2000)
     lat.step(a.warmup)
     clocks = Clocks(local)
     if world > 1:
@@ -359,8 +448,23 @@ def run_ours(a):
         ms = reduce_max(ms, device="cuda")
         torch.distributed.barrier()
     value = world * w.nodes * a.steps / (ms / 1e3) / 1e6
+    coeff = None
+    if rank == 0:
+        t_o, f_o = load_prefix(w.name)
+        coeff = {"timed_run": coeff_errors(lat, w, t_o, f_o)}
     rl = kernel_roofline(torch, lat, w, storage, min(a.steps, 2000), peak)
     lat.close()
+    if rank == 0:
+        coeff["prefix"] = [prefix_accuracy(binding, w, storage, local)]
+        if not a.no_variants:
+            coeff["prefix"] += [prefix_accuracy(binding, w, "f32", local),
+                                prefix_accuracy(binding, inputs.PRECISION, "f32dev", local),
+                                prefix_accuracy(binding, inputs.PRECISION, "f16dev", local)]
+        coeff["definition"] = ("C = 2F/(rho0 u_in^2 chord), every scheme, against the stored FP64 "
+                               "oracle series; per_step: max over the compared steps of |dC| / S(t), "
+                               "S(t) = max over compared steps s >= min(t, n/2) of max(|C_d(s)|, "
+                               "|C_l(s)|); mean: "
+                               "back half of the compared steps, |d mean| / max(|mean C_d|, |mean C_l|)")
 
     # -- end to end through the public API from pinned host buffers
     pm = torch.empty((w.ny, w.nx), dtype=torch.uint8, pin_memory=True)
@@ -397,9 +501,9 @@ def run_ours(a):
                     variant(torch, binding, w, "f16dev", 4000, peak, local),
                     variant(torch, binding, inputs.PRECISION, "f16dev", 2000, peak, local),
                     variant(torch, binding, inputs.PRECISION, "f32dev", 1000, peak, local)]
-        adjoint = [adjoint_variant(torch, binding, inputs.DIFF, "f32", 4000, 1000, local),
-                   adjoint_variant(torch, binding, w, "f32", 1000, 500, local)]
-        batch = [batch_variant(torch, binding, inputs, 256, "f32", 2000, peak, local),
+        adjoint = [adjoint_variant(torch, binding, inputs.DIFF, inputs.DIFF.storage, 4000, 1000, local),
+                   adjoint_variant(torch, binding, w, w.storage, 1000, 500, local)]
+        batch = [batch_variant(torch, binding, inputs, 256, "f32dev", 2000, peak, local),
                  batch_variant(torch, binding, inputs, 256, "f16dev", 2000, peak, local)]
         from paper_2210_10377_gb300 import cylinder
         t0 = time.perf_counter()
@@ -432,11 +536,12 @@ def run_ours(a):
                        "parallelism": "replicas%d" % world},
             "roofline": {"bound": "hbm", "achieved": round(rl["achieved"], 1), "peak": peak,
                          "unit": "GB/s", "frac": round(rl["frac"], 4), "traffic": traffic,
-                         "kernel": "k_collide_stream<f32>", "peak_source": peak_kind,
+                         "kernel": "k_collide_stream<%s>" % storage, "peak_source": peak_kind,
                          "avg_launch_us": round(rl["avg_launch_us"], 2),
                          "algorithmic_bytes_per_launch": rl["algorithmic_bytes"],
                          "link_kernel_us": round(rl["link_kernel_us"], 2)},
             "cpu_baseline": cpu,
+            "coeff_error": coeff,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -514,9 +619,20 @@ def run_profile(a):
         b.close()
         return 0
     w = inputs.WORKLOADS[a.workload] if a.workload else inputs.LARGE_F32
+    if a.shrink > 1:
+        w = inputs.scaled(w, a.shrink)
     storage = a.storage or w.storage
     torch.cuda.set_device(0)
     lat = binding.Lattice(naca_mask_device(w), w.tau, w.u_in, storage=storage, kernel=a.kernel)
+    if a.adjoint:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, dtau, _, _ = lat.adjoint(a.adjoint, max(1, a.adjoint // 2), 1.0, 0.0, want_df0=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": w.name, "storage": storage, "adjoint_steps": a.adjoint,
+                          "ms": round((time.perf_counter() - t0) * 1e3, 2), "J": J, "dJ_dtau": dtau}), flush=True)
+        lat.close()
+        return 0
     lat.step(a.warmup)
     ms = time_steps(torch, lat, a.steps)
     print(json.dumps({"workload": w.name, "storage": storage, "kernel": a.kernel, "steps": a.steps,

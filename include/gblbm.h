@@ -158,6 +158,24 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
  * (an internal invariant; the row is dropped rather than written). */
 lbm_status lbm_step(lbm_ctx *h, int n);
 
+/* lbm_step without the wait: queues n >= 0 steps on the handle's stream and
+ * returns.  The steps' status (EUNSTABLE, ETIMEOUT, ESTATE as for lbm_step,
+ * collected over every step queued since the last wait) is returned by the
+ * next lbm_sync, lbm_step or any call that reads results, each of which first
+ * waits for the queued steps.  The state and the series are those lbm_step
+ * gives.  EINVAL for n < 0; ENOMEM/ECUDA when the work cannot be queued. */
+lbm_status lbm_step_async(lbm_ctx *h, int n);
+
+/* Wait for the steps queued by lbm_step_async and return their status. */
+lbm_status lbm_sync(lbm_ctx *h);
+
+/* Optional: make the next n steps launch-only.  Grows the force series to
+ * hold n more steps and builds the captured step graphs for every starting
+ * buffer, so that a following lbm_step(m <= n) does no allocation, stream
+ * capture or graph instantiation, only launches.  (lbm_step does the same work
+ * lazily when it is not called.)  Blocks.  EINVAL for n < 0; ENOMEM, ECUDA. */
+lbm_status lbm_prepare(lbm_ctx *h, long n);
+
 /* Force on the body (+x downstream) of the last completed step t = T-1
  * (the transition T-1 -> T) for one lbm_scheme.  ESTATE before the first step. */
 lbm_status lbm_force(lbm_ctx *h, int scheme, double *fx, double *fy);
@@ -166,6 +184,19 @@ lbm_status lbm_force(lbm_ctx *h, int scheme, double *fx, double *fy);
  * EINVAL if the range is not kept (record_series = 0 keeps the last two). */
 lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, double *fx,
                             double *fy);
+
+/* Drag and lift coefficients of one lbm_scheme over steps [first, first+count)
+ * (Section V: C_d = 2 F_x / (rho0 U^2 L), C_l = 2 F_y / (rho0 U^2 L), signed,
+ * F the force on the body of that step, rho0 the handle's, L = length the
+ * reference length (the chord; the diameter for a cylinder, Section VI), U =
+ * u_ref the reference speed (u_in)).  Computed on the device from the stored
+ * series.  cd[count], cl[count]: per-step values (either may be NULL);
+ * stats[4] (may be NULL): the window's mean C_d, mean C_l, and the standard
+ * deviations of C_d and C_l (population form, mean removed first), summed in
+ * a fixed order.  EINVAL for an empty or unkept range, length <= 0 or
+ * u_ref = 0. */
+lbm_status lbm_coefficients(lbm_ctx *h, int scheme, long first, long count, double length, double u_ref,
+                            double *cd, double *cl, double *stats);
 
 /* Pre-collision populations f(x, T) as double [9][ny][nx]; solid nodes read 0.
  * For deviation storage the base w_i rho0 is added back in FP64. */
@@ -229,6 +260,20 @@ long lbm_steps_done(const lbm_ctx *h);
 /* Number of fluid-solid links. */
 long lbm_num_links(const lbm_ctx *h);
 
+/* Choose the collide-stream kernel of later steps: 0 = direct loads, 1 = the
+ * staged kernel (bulk tensor copies through an mbarrier pipeline), which needs
+ * a handle created with lbm_bc.kernel = 1 (EINVAL otherwise).  Both do the
+ * same arithmetic per node.  Waits for the handle's stream. */
+lbm_status lbm_set_kernel(lbm_ctx *h, int kernel);
+
+/* Bound, in polls, on each pipeline wait of the staged kernel (default
+ * 2^22; polls < 0 restores it).  For testing the timeout path: with 0, every
+ * CTA's first wait gives up at once, the CTA waits (with a bound of its own)
+ * for the copies it has issued, and lbm_step returns ETIMEOUT; the step's
+ * output is then incomplete, and the caller restores a state
+ * (lbm_set_populations) before stepping on.  Waits for the handle's stream. */
+lbm_status lbm_set_wait_limit(lbm_ctx *h, long polls);
+
 /* Kernel timing for measurements: while on, lbm_step launches each kernel
  * separately (no CUDA graph) between CUDA events on the handle's stream and
  * accumulates device time per kernel.  lbm_kernel_times writes, for
@@ -255,16 +300,21 @@ long lbm_launch_count(const lbm_ctx *h);
  *   d_links     device pointer to cap int32 entries, caller-owned; receives
  *               n*8 + (i-1) in ascending order (at most cap entries).
  *   count       host pointer; receives the total number of links.
- *   cuda_stream cudaStream_t the work is queued on (NULL: legacy default);
- *               the call returns after that stream has finished the work.
+ *   cuda_stream cudaStream_t the work is queued on (NULL: legacy default).
+ * The call is synchronous: it reads the total back into host memory and
+ * returns after that stream has finished the work.  It therefore cannot be
+ * recorded into a CUDA graph, and a stream that is being captured is refused
+ * with EINVAL.  If cap < *count, only the first cap links are written and
+ * *count still receives the full total.
  * Limit: nx*ny <= 2^26 nodes; larger grids return EINVAL.  Working memory is
  * one fixed static device array of 256 KB, present on every device that loads
- * the library until the process exits.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress, with the device current);
- * make that first call before any stream capture.  All calls on a device share
- * the array, so calls whose GPU work overlaps (other host threads, other
- * streams) race and must be serialised by the caller.  Calls no cudaMalloc,
- * cudaFree or other allocating routine. */
+ * the library until the process exits.  Every call looks up that array's
+ * device address (cudaGetSymbolAddress, with the caller's device current), so
+ * a cudaDeviceReset between calls leaves no stale address.  All calls on a
+ * device share the array and every call rewrites what it reads, so calls whose
+ * GPU work overlaps (other host threads, other streams) race and must be
+ * serialised by the caller.  Calls no cudaMalloc, cudaFree or other allocating
+ * routine. */
 lbm_status lbm_links_noalloc(const uint8_t *d_mask, int nx, int ny, int periodic_x,
                              int32_t *d_links, long cap, long *count, void *cuda_stream);
 
@@ -343,6 +393,17 @@ lbm_status lbm_batch_forces(lbm_batch *b, int scheme, long step, double *fx, dou
 /* Force series of one domain, steps [first, first+count): as lbm_force_series. */
 lbm_status lbm_batch_force_series(lbm_batch *b, int domain, int scheme, long first, long count,
                                   double *fx, double *fy);
+
+/* Drag and lift coefficients of one domain over steps [first, first+count): as
+ * lbm_coefficients, with that domain's force series. */
+lbm_status lbm_batch_coefficients(lbm_batch *b, int domain, int scheme, long first, long count, double length,
+                                  double u_ref, double *cd, double *cl, double *stats);
+
+/* Optional: make the next n batch steps launch-only (as lbm_prepare): grows
+ * the series and builds the captured step graphs of both starting buffers for
+ * the current launch configuration (a later lbm_batch_set_launch or
+ * lbm_batch_autotune that changes it drops them again). */
+lbm_status lbm_batch_prepare(lbm_batch *b, long n);
 
 /* Pre-collision populations of one domain at the current step: out is double
  * [9][ny][nx] of that domain (0 at solid nodes), as lbm_populations. */

@@ -86,9 +86,16 @@ def lib():
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_prepare.argtypes = [vp, C.c_long]
+    L.lbm_step_async.argtypes = [vp, C.c_int]
+    L.lbm_sync.argtypes = [vp]
+    L.lbm_set_kernel.argtypes = [vp, C.c_int]
+    L.lbm_set_wait_limit.argtypes = [vp, C.c_long]
+    L.lbm_coefficients.argtypes = [vp, C.c_int, C.c_long, C.c_long, C.c_double, C.c_double, dp, dp, dp]
     for name in ("lbm_create", "lbm_step", "lbm_force", "lbm_force_series", "lbm_populations",
                  "lbm_set_populations", "lbm_links", "lbm_control_volume", "lbm_naca_mask",
-                 "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_adjoint"):
+                 "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_adjoint", "lbm_prepare",
+                 "lbm_coefficients", "lbm_set_kernel", "lbm_set_wait_limit", "lbm_step_async", "lbm_sync"):
         getattr(L, name).restype = C.c_int
     # batches
     L.lbm_batch_create.argtypes = [C.POINTER(lbm_domain), C.c_int, C.POINTER(lbm_bc), C.POINTER(vp)]
@@ -123,10 +130,13 @@ def lib():
     L.lbm_batch_pressure_coefficient.restype = C.c_int
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
+    L.lbm_batch_prepare.argtypes = [vp, C.c_long]
+    L.lbm_batch_coefficients.argtypes = [vp, C.c_int, C.c_int, C.c_long, C.c_long, C.c_double, C.c_double,
+                                         dp, dp, dp]
     for name in ("lbm_batch_create", "lbm_batch_step", "lbm_batch_forces", "lbm_batch_force_series",
                  "lbm_batch_populations", "lbm_batch_set_populations", "lbm_batch_status",
                  "lbm_batch_set_launch", "lbm_batch_get_launch", "lbm_batch_shape",
-                 "lbm_batch_autotune"):
+                 "lbm_batch_autotune", "lbm_batch_prepare", "lbm_batch_coefficients"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -258,6 +268,14 @@ class Lattice:
     def step(self, n=1):
         _check(lib().lbm_step(self._h, int(n)), self._h)
 
+    def step_async(self, n=1):
+        """Queue n steps without waiting (lbm_step_async); sync() or any call
+        that reads results waits for them and reports their status."""
+        _check(lib().lbm_step_async(self._h, int(n)), self._h)
+
+    def sync(self):
+        _check(lib().lbm_sync(self._h), self._h)
+
     def force(self, scheme):
         fx, fy = C.c_double(), C.c_double()
         _check(lib().lbm_force(self._h, SCHEMES.get(scheme, scheme), C.byref(fx), C.byref(fy)),
@@ -272,6 +290,35 @@ class Lattice:
         _check(lib().lbm_force_series(self._h, SCHEMES.get(scheme, scheme), int(first),
                                       int(count), _dp(fx), _dp(fy)), self._h)
         return fx[:count], fy[:count]
+
+    def prepare(self, n):
+        """Grow the series for n more steps and build every captured step graph
+        (lbm_prepare), so that stepping afterwards only launches."""
+        _check(lib().lbm_prepare(self._h, int(n)), self._h)
+
+    def set_kernel(self, kernel):
+        """'direct' or 'staged' for later steps (lbm_set_kernel)."""
+        _check(lib().lbm_set_kernel(self._h, {"direct": 0, "staged": 1}.get(kernel, kernel)), self._h)
+
+    def set_wait_limit(self, polls):
+        """Poll bound of the staged kernel's pipeline waits (lbm_set_wait_limit;
+        negative: the default).  Only for testing the timeout path."""
+        _check(lib().lbm_set_wait_limit(self._h, int(polls)), self._h)
+
+    def coefficients(self, scheme, length, u_ref, first=0, count=None, per_step=True):
+        """Drag and lift coefficients of one scheme over steps [first,
+        first+count) (lbm_coefficients): (cd[count], cl[count], stats) with
+        stats = (mean C_d, mean C_l, std C_d, std C_l); cd and cl are None
+        when per_step is false."""
+        if count is None:
+            count = self.steps_done - first
+        cd = np.zeros(max(count, 1)) if per_step else None
+        cl = np.zeros(max(count, 1)) if per_step else None
+        st = np.zeros(4)
+        _check(lib().lbm_coefficients(self._h, SCHEMES.get(scheme, scheme), int(first), int(count),
+                                      float(length), float(u_ref), _dp(cd) if per_step else None,
+                                      _dp(cl) if per_step else None, _dp(st)), self._h)
+        return (cd[:count] if per_step else None), (cl[:count] if per_step else None), tuple(st)
 
     # -- state
     def populations(self, out=None):
@@ -429,6 +476,25 @@ class Batch:
         _bcheck(lib().lbm_batch_force_series(self._h, int(domain), sc, int(first), int(count),
                                              _dp(fx), _dp(fy)), self._h)
         return fx, fy
+
+    def prepare(self, n):
+        """Grow the series for n more steps and build the captured step graphs
+        of the current launch configuration (lbm_batch_prepare)."""
+        _bcheck(lib().lbm_batch_prepare(self._h, int(n)), self._h)
+
+    def coefficients(self, domain, scheme, length, u_ref, first=0, count=None, per_step=False):
+        """Drag and lift coefficients of one domain (lbm_batch_coefficients):
+        (cd, cl, stats) as Lattice.coefficients."""
+        if count is None:
+            count = self.steps_done - first
+        cd = np.zeros(max(count, 1)) if per_step else None
+        cl = np.zeros(max(count, 1)) if per_step else None
+        st = np.zeros(4)
+        sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        _bcheck(lib().lbm_batch_coefficients(self._h, int(domain), sc, int(first), int(count), float(length),
+                                             float(u_ref), _dp(cd) if per_step else None,
+                                             _dp(cl) if per_step else None, _dp(st)), self._h)
+        return (cd[:count] if per_step else None), (cl[:count] if per_step else None), tuple(st)
 
     def populations(self, domain):
         ny, nx = self.shapes[domain]

@@ -17,48 +17,13 @@
 //   dJ/du_in(y) += sum_i lt_i rho0 w_i (3 c_ix + 9 c_ix^2 u - 3 u) and lam = 0.
 // (feq here is the second-order equilibrium of Section II written in rho and
 // j = rho u; BGK: ft = f + w (feq - f).)
-#include "lbm_internal.cuh"
+#include "lbm_device.cuh"
 
 namespace gblbm {
 
-// Pre-collision f(t) of every fluid node, in the compute type, from a state
-// buffer (post-collision ft(t-1) to be pulled, or f(t) itself when
-// precollision): pull with bounce-back and the outlet copy of column nx-2.
-// The inlet column is left untouched (the adjoint does not read it).
-template <int S>
-__global__ void k_precollision(const typename Traits<S>::store_t *__restrict__ src,
-                               const uint16_t *__restrict__ nbits, long long plane, int nx, int ny,
-                               int pitch, int precollision, typename Traits<S>::comp_t *__restrict__ out)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= nx || x == 0) return;
-    const long long idx = (long long)y * pitch + x;
-    if (nbits[idx] & 1) return;
-    if (precollision) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) out[i * plane + idx] = to_comp(src[i * plane + idx]);
-        return;
-    }
-    const int xs = x == nx - 1 ? nx - 2 : x;
-    const long long sidx = (long long)y * pitch + xs;
-    const uint16_t nbs = nbits[sidx];
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int sx = xs - cx(i);
-        const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
-        typename Traits<S>::comp_t v;
-        if (nbs & (1u << opp(i)))
-            v = to_comp(src[opp(i) * plane + sidx]);
-        else
-            v = to_comp(src[i * plane + (long long)sy * pitch + sx]);
-        out[i * plane + idx] = v;
-    }
-}
-
 struct AdjArgs {
-    const void *fpre;      // [9][ny][pitch] compute type: f(t) (deviations for deviation storage)
+    const void *src;       // [9][ny][pitch] storage type: ft(t-1) (f(t) itself when precollision)
+    int precollision;
     const void *lam_next;  // [9][ny][pitch] compute type: lam(t+1)
     void *lam;             // [9][ny][pitch] compute type: lam(t)
     const uint16_t *nbits;
@@ -90,10 +55,13 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs a)
     constexpr bool DEV = Traits<S>::dev;
     const T *__restrict__ lamn = (const T *)a.lam_next;
     T *__restrict__ lam = (T *)a.lam;
-    const T *__restrict__ fp = (const T *)a.fpre;
+    using ST = typename Traits<S>::store_t;
+    const ST *__restrict__ src = (const ST *)a.src;
+    using Acc = typename AccOf<S>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    double dw = 0.0;
+    Acc dw;
+    acc_zero(dw);
     if (x < a.nx) {
         const long long idx = (long long)y * a.pitch + x;
         const uint16_t nb = a.nbits[idx];
@@ -129,15 +97,33 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs a)
 #pragma unroll
                 for (int i = 0; i < 9; ++i) lam[i * a.plane + idx] = T(0);
             } else {
+                // f(t) of the step, pulled from the stored ft(t-1) of the
+                // segment's recomputed forward: halfway bounce-back from the
+                // node's own opposite population, and the outlet column
+                // x = nx-1 taking the pull of column nx-2
                 T g[9];
+                if (a.precollision) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) g[i] = fp[i * a.plane + idx];
+                    for (int i = 0; i < 9; ++i) g[i] = to_comp(src[i * a.plane + idx]);
+                } else {
+                    const int xs = x == a.nx - 1 ? a.nx - 2 : x;
+                    const long long sidx = (long long)y * a.pitch + xs;
+                    const uint16_t nbs = xs == x ? nb : a.nbits[sidx];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
+                        g[i] = (nbs & (1u << opp(i)))
+                                   ? to_comp(src[opp(i) * a.plane + sidx])
+                                   : to_comp(src[i * a.plane + (long long)sy * a.pitch + (xs - cx(i))]);
+                    }
+                }
                 const T R0 = DEV ? (T)a.rho0 : T(0);
                 const T jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
                 const T jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
                 const T drho = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
                 const T rho = R0 + drho;
-                const T ux = jx / rho, uy = jy / rho;
+                const T inv = T(1) / rho;
+                const T ux = jx * inv, uy = jy * inv;
                 const T usq = ux * ux + uy * uy;
                 const T om = (T)a.omega;
                 T A = T(0), Bx = T(0), By = T(0), dwt = T(0);
@@ -154,15 +140,17 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs a)
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
                     lam[k * a.plane + idx] = (T(1) - om) * lt[k] + om * (A + Bx * T(cx(k)) + By * T(cy(k)));
-                dw = (double)dwt;
+                dw = as_acc(dwt, Acc());
             }
         }
     }
-    // per-block running sum of dJ/domega (fixed order: warp shuffles, then warps)
+    // per-block running sum of dJ/domega (fixed order: warp shuffles, then
+    // warps); float-float below FP64 storage, so that the one-per-node part
+    // of the sum stays off this GPU's few FP64 units
     __shared__ double ws[8];
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) dw += __shfl_down_sync(0xffffffffu, dw, d);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = dw;
+    for (int d = 16; d > 0; d >>= 1) acc_add(dw, shfl_down(dw, d));
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc_double(dw);
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -180,42 +168,17 @@ __global__ void k_sum_serial(const double *__restrict__ v, long long n, double *
     *out = s;
 }
 
-cudaError_t launch_precollision(int storage, const void *src, const uint16_t *nbits, long long plane,
-                                int nx, int ny, int pitch, int precollision, void *out,
-                                cudaStream_t st)
-{
-    dim3 grid((nx + 255) / 256, ny);
-    switch (storage) {
-    case LBM_F64:
-        k_precollision<LBM_F64><<<grid, 256, 0, st>>>((const double *)src, nbits, plane, nx, ny, pitch,
-                                                      precollision, (double *)out);
-        break;
-    case LBM_F32:
-        k_precollision<LBM_F32><<<grid, 256, 0, st>>>((const float *)src, nbits, plane, nx, ny, pitch,
-                                                      precollision, (float *)out);
-        break;
-    case LBM_F32_DEV:
-        k_precollision<LBM_F32_DEV><<<grid, 256, 0, st>>>((const float *)src, nbits, plane, nx, ny,
-                                                          pitch, precollision, (float *)out);
-        break;
-    default:
-        k_precollision<LBM_F16_DEV><<<grid, 256, 0, st>>>((const __half *)src, nbits, plane, nx, ny,
-                                                          pitch, precollision, (float *)out);
-        break;
-    }
-    return cudaGetLastError();
-}
-
 int adjoint_blocks(int nx, int ny) { return ((nx + 255) / 256) * ny; }
 
-cudaError_t launch_adjoint_step(int storage, const void *fpre, const void *lam_next, void *lam,
+cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, const void *lam_next, void *lam,
                                 const uint16_t *nbits, const double *u_row, double *du_acc,
                                 double *dw_acc, long long plane, int nx, int ny, int pitch,
                                 int in_window, double omega, double rho0, double obj_x,
                                 double obj_y, cudaStream_t st)
 {
     AdjArgs a;
-    a.fpre = fpre;
+    a.src = src;
+    a.precollision = precollision;
     a.lam_next = lam_next;
     a.lam = lam;
     a.nbits = nbits;

@@ -52,6 +52,7 @@ struct lbm_ctx {
     bool tmap_ok = false;
     int use_bulk = 0, sm_count = 1;
     int pf_rows = 0;                                     // L2 prefetch distance of the direct kernel
+    unsigned int wait_limit = WAIT_LIMIT;                // polls of each staged-kernel pipeline wait
     int cur = 0;                 // buffer holding the latest state
     cudaStream_t side = nullptr; // link kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_read[NBUF] = {nullptr, nullptr, nullptr};
@@ -75,6 +76,9 @@ struct lbm_ctx {
     double *carry = nullptr;     // [8]
     long long *step_ctr = nullptr;
     int *status = nullptr;       // [2]
+    int status_host[2] = {0, 0};  // the status words read back by settle
+    bool status_armed = false;   // status cleared for the queued steps
+    bool pending = false;        // steps queued and not yet settled
     long long t = 0;
     int precollision = 1;
     long long carry_from = 0;    // first step of the current DRTT chain
@@ -210,6 +214,7 @@ StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
     a.use_bulk = h->use_bulk;
     a.sm_count = h->sm_count;
     a.pf_rows = h->pf_rows;
+    a.wait_limit = h->wait_limit;
     return a;
 }
 
@@ -635,16 +640,21 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     return LBM_OK;
 }
 
-lbm_status lbm_step(lbm_ctx *h, int n)
+namespace {
+
+// Queues n steps on the handle's stream without waiting for them.  The
+// status words are cleared before the first queued step after a settle and
+// then collect the flags of every step until the next settle.
+lbm_status queue_steps(lbm_ctx *h, int n)
 {
-    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
-    if (n < 0) return set_err(h, LBM_EINVAL, "n must be >= 0");
-    if (n == 0) return LBM_OK;
     lbm_status st = ensure_series(h, h->t + n);
     if (st != LBM_OK) return st;
-    const int status0[2] = {0, INT_MAX};
-    CK(h, cudaMemcpyAsync(h->status, status0, sizeof(status0), cudaMemcpyHostToDevice, h->stream),
-       "H2D status");
+    if (!h->status_armed) {
+        // status[0] = 0 (no flag), status[1] = 0x7f7f7f7f (no bad step yet)
+        CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
+        CK(h, cudaMemsetAsync(h->status + 1, 0x7f, sizeof(int), h->stream), "status reset");
+        h->status_armed = true;
+    }
     if (h->timing && (int)h->events.size() < 3 * TIMING_BATCH) {
         h->events.resize(3 * TIMING_BATCH, nullptr);
         for (auto &e : h->events)
@@ -684,10 +694,20 @@ lbm_status lbm_step(lbm_ctx *h, int n)
         st = flush_timing(h, nev);
         if (st != LBM_OK) return st;
     }
-    int status[2];
-    CK(h, cudaMemcpyAsync(status, h->status, sizeof(status), cudaMemcpyDeviceToHost, h->stream),
+    h->pending = true;
+    return LBM_OK;
+}
+
+// Waits for the queued steps and turns their status words into a result.
+lbm_status settle(lbm_ctx *h)
+{
+    if (!h->pending) return LBM_OK;
+    h->pending = false;
+    h->status_armed = false;
+    CK(h, cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream),
        "D2H status");
     CK(h, cudaStreamSynchronize(h->stream), "step sync");
+    const int *status = h->status_host;
     if (h->t - 1 > h->carry_from) h->drtt_ready = h->t - 1 > h->drtt_ready ? h->t - 1 : h->drtt_ready;
     if (status[0] & 4)
         return set_err(h, LBM_ESTATE, "a force-series row lay beyond the series buffer");
@@ -697,9 +717,43 @@ lbm_status lbm_step(lbm_ctx *h, int n)
     return LBM_OK;
 }
 
+#define SETTLE(h)                          \
+    do {                                   \
+        lbm_status s_ = settle(h);         \
+        if (s_ != LBM_OK) return s_;       \
+    } while (0)
+
+}  // namespace
+
+lbm_status lbm_step(lbm_ctx *h, int n)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (n < 0) return set_err(h, LBM_EINVAL, "n must be >= 0");
+    SETTLE(h);
+    if (n == 0) return LBM_OK;
+    lbm_status st = queue_steps(h, n);
+    if (st != LBM_OK) return st;
+    return settle(h);
+}
+
+lbm_status lbm_step_async(lbm_ctx *h, int n)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (n < 0) return set_err(h, LBM_EINVAL, "n must be >= 0");
+    if (n == 0) return LBM_OK;
+    return queue_steps(h, n);
+}
+
+lbm_status lbm_sync(lbm_ctx *h)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    return settle(h);
+}
+
 lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, double *fx, double *fy)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     if (scheme < 0 || scheme > LBM_FORCE_SI) return set_err(h, LBM_EINVAL, "unknown scheme %d", scheme);
     if (count < 0 || first < 0 || first + count > h->t)
         return set_err(h, LBM_EINVAL, "steps [%ld, %ld) outside [0, %lld)", first, first + count, h->t);
@@ -732,9 +786,90 @@ lbm_status lbm_force_series(lbm_ctx *h, int scheme, long first, long count, doub
     return LBM_OK;
 }
 
+lbm_status lbm_set_kernel(lbm_ctx *h, int kernel)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
+    if (kernel != 0 && kernel != 1) return set_err(h, LBM_EINVAL, "unknown kernel choice %d", kernel);
+    if (kernel == 1 && !h->tmap_ok)
+        return set_err(h, LBM_EINVAL, "the staged kernel needs a handle created with kernel = 1");
+    if ((kernel == 1) != (h->use_bulk != 0)) {
+        CK(h, cudaStreamSynchronize(h->stream), "sync");
+        drop_graphs(h);
+        h->use_bulk = kernel;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wait_limit(lbm_ctx *h, long polls)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
+    const unsigned int lim = polls < 0 ? WAIT_LIMIT : (polls > (long)WAIT_LIMIT ? WAIT_LIMIT : (unsigned int)polls);
+    if (lim != h->wait_limit) {
+        CK(h, cudaStreamSynchronize(h->stream), "sync");
+        drop_graphs(h);
+        h->wait_limit = lim;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_prepare(lbm_ctx *h, long n)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
+    if (n < 0) return set_err(h, LBM_EINVAL, "n must be >= 0");
+    lbm_status st = ensure_series(h, h->t + n);
+    if (st != LBM_OK) return st;
+    for (int p = 0; p < NBUF; ++p)
+        for (int k = 0; k < 2; ++k)
+            if (!h->graph[p][k]) {
+                st = build_graph(h, p, k);
+                if (st != LBM_OK) return st;
+            }
+    return LBM_OK;
+}
+
+lbm_status lbm_coefficients(lbm_ctx *h, int scheme, long first, long count, double length, double u_ref,
+                            double *cd, double *cl, double *stats)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
+    if (scheme < 0 || scheme > LBM_FORCE_SI) return set_err(h, LBM_EINVAL, "unknown scheme %d", scheme);
+    if (count < 1 || first < 0 || first + count > h->t)
+        return set_err(h, LBM_EINVAL, "steps [%ld, %ld) outside [0, %lld) or empty", first, first + count, h->t);
+    if (!(length > 0) || !std::isfinite(length) || !(u_ref != 0) || !std::isfinite(u_ref))
+        return set_err(h, LBM_EINVAL, "length must be > 0 and u_ref nonzero, both finite");
+    if (!h->record_series && first < h->t - 2)
+        return set_err(h, LBM_EINVAL, "only the last two steps are kept (record_series = 0)");
+    if (scheme == LBM_FORCE_DRTT && first + count > h->drtt_ready) {
+        lbm_status st = finalize_drtt(h);
+        if (st != LBM_OK) return st;
+    }
+    const double norm = 2.0 / (h->rho0 * u_ref * u_ref * length);
+    const bool per_step = cd || cl;
+    double *out = (double *)dev_alloc(h, sizeof(double) * (4 + (per_step ? 2 * (size_t)count : 0)));
+    if (!out) return set_err(h, LBM_ENOMEM, "coefficient buffer allocation failed");
+    cudaError_t e = launch_coefficients(h->series, SERIES_ROW, 2 * scheme, first, count, !h->record_series, norm,
+                                        out, per_step, h->stream);
+    double st4[4];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st4, out, sizeof(st4), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && cd)
+        e = cudaMemcpyAsync(cd, out + 4, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && cl)
+        e = cudaMemcpyAsync(cl, out + 4 + count, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, out);
+    h->launches += 1;
+    if (e != cudaSuccess) return cuda_err(h, e, "coefficients");
+    if (stats) memcpy(stats, st4, sizeof(st4));
+    return LBM_OK;
+}
+
 lbm_status lbm_force(lbm_ctx *h, int scheme, double *fx, double *fy)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     if (h->t < 1) return set_err(h, LBM_ESTATE, "no step has been taken");
     return lbm_force_series(h, scheme, (long)(h->t - 1), 1, fx, fy);
 }
@@ -742,6 +877,7 @@ lbm_status lbm_force(lbm_ctx *h, int scheme, double *fx, double *fy)
 lbm_status lbm_populations(lbm_ctx *h, double *out)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     if (!out) return set_err(h, LBM_EINVAL, "out must not be NULL");
     const size_t N = (size_t)h->nx * h->ny;
     double *scratch = (double *)dev_alloc(h, sizeof(double) * N);
@@ -765,6 +901,7 @@ lbm_status lbm_populations(lbm_ctx *h, double *out)
 lbm_status lbm_set_populations(lbm_ctx *h, const double *in)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     if (!in) return set_err(h, LBM_EINVAL, "in must not be NULL");
     const size_t N = (size_t)h->nx * h->ny;
     for (size_t k = 0; k < 9 * N; ++k)
@@ -800,6 +937,7 @@ lbm_status lbm_pressure_coefficient(lbm_ctx *h, double p_inf, double q, int32_t 
                                     long *count)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     if (!std::isfinite(p_inf) || !std::isfinite(q) || q == 0.0)
         return set_err(h, LBM_EINVAL, "p_inf must be finite and q finite and nonzero");
     if (count) *count = (long)h->n_bnodes;
@@ -889,6 +1027,7 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
                        double *J, double *dJ_dtau, double *dJ_du, double *dJ_df0)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     if (steps < 1 || window < 1 || window > steps)
         return set_err(h, LBM_EINVAL, "need 1 <= window <= steps (got %d, %d)", window, steps);
     if (h->periodic) return set_err(h, LBM_EINVAL, "the adjoint covers the channel set-up only");
@@ -920,17 +1059,17 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
         for (void *p : owned) dev_free(h, p);
         owned.clear();
     };
+    // checkpoints; the recomputed post-collision states of one segment (the
+    // first step of a segment reads its checkpoint, step s > 0 the state
+    // written by step s-1, so K-1 buffers); the adjoint pair lam(t+1), lam(t)
     char *ck = (char *)grab(buf_bytes * nck);
-    char *seg = (char *)grab(comp_bytes * K);
+    char *seg = K > 1 ? (char *)grab(buf_bytes * (K - 1)) : nullptr;
     char *lam_a = (char *)grab(comp_bytes), *lam_b = (char *)grab(comp_bytes);
-    const size_t guard_front = 256, guard_back = 2048;
-    char *sbase0 = (char *)grab(guard_front + buf_bytes + guard_back);
-    char *sbase1 = (char *)grab(guard_front + buf_bytes + guard_back);
     double *part = (double *)grab(sizeof(double) * CV_PARTIAL * h->n_cv_tiles);
     double *du_acc = (double *)grab(sizeof(double) * h->ny);
     double *dw_acc = (double *)grab(sizeof(double) * nblk);
     double *dw_out = (double *)grab(sizeof(double));
-    if (!ck || !seg || !lam_a || !lam_b || !sbase0 || !sbase1 || !part || !du_acc || !dw_acc || !dw_out) {
+    if (!ck || (K > 1 && !seg) || !lam_a || !lam_b || !part || !du_acc || !dw_acc || !dw_out) {
         release();
         return set_err(h, LBM_ENOMEM, "adjoint: allocation of checkpoints / work arrays failed");
     }
@@ -971,38 +1110,26 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
     if (e == cudaSuccess) e = cudaMemsetAsync(lam_a, 0, comp_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(du_acc, 0, sizeof(double) * h->ny, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dw_acc, 0, sizeof(double) * nblk, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sbase0, 0, guard_front + buf_bytes + guard_back, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sbase1, 0, guard_front + buf_bytes + guard_back, st);
     char *lam_next = lam_b, *lam_cur = lam_a;  // lam(T) = 0
     const double obj_x = 2.0 * wx / window, obj_y = 2.0 * wy / window;
     for (int k = nck - 1; k >= 0 && e == cudaSuccess; --k) {
         const int t0 = k * K;
         const int n = (k + 1) * K <= steps ? K : steps - t0;
-        char *s_cur = sbase0 + guard_front, *s_nxt = sbase1 + guard_front;
-        e = cudaMemcpyAsync(s_cur, ck + buf_bytes * k, buf_bytes, cudaMemcpyDeviceToDevice, st);
-        int pre = ckpre[k];
-        for (int s = 0; s < n && e == cudaSuccess; ++s) {
-            e = launch_precollision(h->storage, s_cur, h->nbits, h->plane, h->nx, h->ny, h->pitch, pre,
-                                    seg + comp_bytes * s, st);
-            if (e == cudaSuccess && s + 1 < n) {
-                StepArgs sa = step_args(h, h->cur, next_buf(h->cur), pre);
-                sa.src = s_cur;
-                sa.dst = s_nxt;
-                sa.partials = part;
-                sa.use_bulk = 0;
-                e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false, nullptr, st);
-                char *tmp = s_cur;
-                s_cur = s_nxt;
-                s_nxt = tmp;
-                pre = 0;
-                h->launches += 1;
-            }
+        // the state step t0 + s reads
+        auto state = [&](int s) { return s == 0 ? ck + buf_bytes * k : seg + buf_bytes * (s - 1); };
+        for (int s = 0; s + 1 < n && e == cudaSuccess; ++s) {
+            StepArgs sa = step_args(h, h->cur, next_buf(h->cur), s == 0 ? ckpre[k] : 0);
+            sa.src = state(s);
+            sa.dst = state(s + 1);
+            sa.partials = part;
+            sa.use_bulk = 0;
+            e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false, nullptr, st);
             h->launches += 1;
         }
         for (int s = n - 1; s >= 0 && e == cudaSuccess; --s) {
             const int t = t0 + s;
-            e = launch_adjoint_step(h->storage, seg + comp_bytes * s, lam_next, lam_cur, h->nbits, h->u_row,
-                                    du_acc, dw_acc, h->plane, h->nx, h->ny, h->pitch,
+            e = launch_adjoint_step(h->storage, state(s), s == 0 ? ckpre[k] : 0, lam_next, lam_cur, h->nbits,
+                                    h->u_row, du_acc, dw_acc, h->plane, h->nx, h->ny, h->pitch,
                                     t >= steps - window, h->omega, h->rho0, obj_x, obj_y, st);
             char *tmp = lam_next;
             lam_next = lam_cur;
@@ -1053,6 +1180,7 @@ long lbm_num_links(const lbm_ctx *h) { return h ? (long)h->nlinks : -1; }
 lbm_status lbm_set_kernel_timing(lbm_ctx *h, int on)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     h->timing = on != 0;
     return LBM_OK;
 }
@@ -1060,6 +1188,7 @@ lbm_status lbm_set_kernel_timing(lbm_ctx *h, int on)
 lbm_status lbm_kernel_times(lbm_ctx *h, double *ms, long *launches, int reset)
 {
     if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    SETTLE(h);
     for (int k = 0; k < 2; ++k) {
         if (ms) ms[k] = h->kt_ms[k];
         if (launches) launches[k] = h->kt_n[k];

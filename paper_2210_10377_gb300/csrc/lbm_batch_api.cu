@@ -7,6 +7,7 @@
 // Two population buffers alternate: step t reads buffer t % 2 and writes the
 // other; the link kernel of step t runs after the collide-stream kernel on the
 // same stream, so the buffer of step t-1 is free again once step t is done.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -24,6 +25,16 @@ using namespace gblbm;
 
 namespace {
 
+// Tiles of a launch ordered by code path or left in domain order, per storage
+// (a tuning knob; measured on the 256-domain recipe: path order takes FP16
+// deviations from 0.549 to 0.579 of the copy bandwidth and FP32 from 0.770
+// down to 0.739, so only FP16 uses it).
+#ifndef GBLBM_BATCH_PATH_ORDER_F16
+#define GBLBM_BATCH_PATH_ORDER_F16 1
+#endif
+#ifndef GBLBM_BATCH_PATH_ORDER_F32
+#define GBLBM_BATCH_PATH_ORDER_F32 0
+#endif
 constexpr int BATCH_GRAPH_STEPS = 16;  // steps per captured graph (even: ends on the start buffer)
 constexpr int BATCH_GRID_CHOICES[] = {1, 2, 3, 4, 6, 8};  // persistent CTAs per SM tried by the tuner
 
@@ -664,6 +675,29 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
                     chk_cv.push_back(make_int4(d % MAX_BATCH_DOMAINS, tx, ty,
                                                flags[foff[d] + (long long)ty * tiles_x + tx] ? 1 : 0));
         }
+        // Within each launch (a chunk of domains), the tiles that take the
+        // interior path come first, then the edge tiles (top and bottom tile
+        // rows, the inlet and outlet tile columns), then the tiles next to a
+        // body.  CTAs start roughly in launch order, so co-resident CTAs then
+        // mostly run the same code, which keeps the instruction caches warm.
+        // Any order gives the same bits: each tile writes its own nodes and
+        // its own partial-sum slot.
+        const bool path_order =
+            b->storage == LBM_F16_DEV ? GBLBM_BATCH_PATH_ORDER_F16 != 0 : GBLBM_BATCH_PATH_ORDER_F32 != 0;
+        for (int c0 = 0; path_order && c0 < n; c0 += MAX_BATCH_DOMAINS) {
+            const int c1 = c0 + MAX_BATCH_DOMAINS < n ? c0 + MAX_BATCH_DOMAINS : n;
+            const long long lo = b->dom[c0].tile_base[sh];
+            const long long hi = c1 < n ? b->dom[c1].tile_base[sh] : (long long)chk.size();
+            auto path = [&](const int4 &t) {
+                const Domain &m = b->dom[c0 + t.x];
+                if (t.w) return 2;
+                const bool edge_row = periodic || t.z == 0 || (t.z + 1) * th >= m.ny;
+                const bool edge_col = t.y == 0 || (t.y + 1) * tw >= m.nx - 1;
+                return edge_row || edge_col ? 1 : 0;
+            };
+            std::stable_sort(chk.begin() + lo, chk.begin() + hi,
+                             [&](const int4 &u, const int4 &v) { return path(u) < path(v); });
+        }
         b->n_tiles[sh] = (long long)chk.size();
         b->n_cv_entries[sh] = (long long)chk_cv.size();
         BALLOC(b->checked[sh], int4 *, sizeof(int4) * (chk.size() > 0 ? chk.size() : 1));
@@ -809,6 +843,52 @@ lbm_status lbm_batch_force_series(lbm_batch *b, int domain, int scheme, long fir
         fx[k] = rows[(size_t)SERIES_ROW * k + 2 * scheme];
         fy[k] = rows[(size_t)SERIES_ROW * k + 2 * scheme + 1];
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_prepare(lbm_batch *b, long n)
+{
+    if (!b) return berr(nullptr, LBM_EINVAL, "NULL handle");
+    if (n < 0) return berr(b, LBM_EINVAL, "n must be >= 0");
+    lbm_status st = ensure_series(b, b->t + n);
+    if (st != LBM_OK) return st;
+    for (int c = 0; c < 2; ++c)
+        for (int k = 0; k < 2; ++k)
+            if (!b->graph[c][k]) {
+                st = build_graph(b, c, k);
+                if (st != LBM_OK) return st;
+            }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_coefficients(lbm_batch *b, int domain, int scheme, long first, long count, double length,
+                                  double u_ref, double *cd, double *cl, double *stats)
+{
+    if (!b) return berr(nullptr, LBM_EINVAL, "NULL handle");
+    if (domain < 0 || domain >= b->n) return berr(b, LBM_EINVAL, "no domain %d", domain);
+    if (count < 1) return berr(b, LBM_EINVAL, "the window must hold at least one step");
+    if (!(length > 0) || !std::isfinite(length) || !(u_ref != 0) || !std::isfinite(u_ref))
+        return berr(b, LBM_EINVAL, "length must be > 0 and u_ref nonzero, both finite");
+    lbm_status st = check_range(b, scheme, first, count);
+    if (st != LBM_OK) return st;
+    const double norm = 2.0 / (b->rho0 * u_ref * u_ref * length);
+    const bool per_step = cd || cl;
+    double *out = (double *)bdev_alloc(b, sizeof(double) * (4 + (per_step ? 2 * (size_t)count : 0)));
+    if (!out) return berr(b, LBM_ENOMEM, "coefficient buffer allocation failed");
+    cudaError_t e = launch_coefficients(b->series + (size_t)SERIES_ROW * domain, (long long)SERIES_ROW * b->n,
+                                        2 * scheme, first, count, !b->record_series, norm, out, per_step,
+                                        b->stream);
+    double st4[4];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st4, out, sizeof(st4), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && cd)
+        e = cudaMemcpyAsync(cd, out + 4, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && cl)
+        e = cudaMemcpyAsync(cl, out + 4 + count, sizeof(double) * count, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    bdev_free(b, out);
+    b->launches += 1;
+    if (e != cudaSuccess) return bcuda(b, e, "coefficients");
+    if (stats) memcpy(stats, st4, sizeof(st4));
     return LBM_OK;
 }
 

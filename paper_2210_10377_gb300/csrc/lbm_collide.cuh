@@ -22,14 +22,17 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
 // ---------------------------------------------------------------------------
 
 // BGK collision (Section II, Eq. CollideAdv): rho = R0 + sum g (R0 = rho0 for
-// deviation storage, g = f - w rho0; R0 = 0 and g = f otherwise), u = (sum c g)
-// / rho, and with theta0 = 1/3 the second-order equilibrium less its base,
-//   feq_i - w_i R0 = w_i (base + 4.5 rho (c_i.u)^2 + 3 rho c_i.u),
-//   base = drho - 1.5 rho u^2,
+// deviation storage, g = f - w rho0; R0 = 0 and g = f otherwise), j = sum c g,
+// u = j / rho, and with theta0 = 1/3 the second-order equilibrium less its
+// base, written with rho u = j,
+//   feq_i - w_i R0 = w_i (base + 4.5 (c_i.j)(c_i.u)) + 3 w_i c_i.j,
+//   base = drho - 1.5 j.u,
 // evaluated for opposite directions together (they share the even part and
-// differ in the sign of the odd one).  The relaxation ft = f + omega (feq - f)
-// is written as (1 - omega) g + (omega w_i)(even +- odd), plus 3 w_i c_i.g with
-// a body force.
+// differ in the sign of the odd one).  The relaxation is ft = g + omega (feq -
+// g), plus 3 w_i c_i.g with a body force.  In exact arithmetic every such
+// form is the same map; in FP32 this one conserves momentum to the last
+// rounding (see Lat and relax_pair_j), which keeps reduced-precision runs on
+// the FP64 trajectory far longer.
 //
 // The FP32 arithmetic is spelled out operation by operation, each rounded
 // once, in one template over the value type: one node (float) or two nodes at
@@ -46,6 +49,7 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float splat(float c) { return c; }
     static __device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+    static __device__ __forceinline__ float neg(float v) { return -v; }
 };
 // FP64 has no packed form, so its operations are left to the compiler (it
 // may fuse a product into the following sum), as in any FP64 expression.
@@ -56,7 +60,13 @@ template <> struct Arith<double> {
     static __device__ __forceinline__ double fma(double a, double b, double c) { return a * b + c; }
     static __device__ __forceinline__ double splat(double c) { return c; }
     static __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
+    static __device__ __forceinline__ double neg(double v) { return -v; }
 };
+// Packed FP32 pairs.  The code generator may fuse a packed product that feeds
+// a packed sum into one packed fma (measured: it does, whatever rounding
+// modifier the two carry), which the one-node form never does; so the
+// collision below never lets a product feed a sum: it writes such pairs as
+// explicit fmas.
 template <> struct Arith<float2> {
     static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
     static __device__ __forceinline__ float2 sub(float2 a, float2 b)
@@ -67,17 +77,41 @@ template <> struct Arith<float2> {
     static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
     static __device__ __forceinline__ float2 splat(float c) { return make_float2(c, c); }
     static __device__ __forceinline__ float2 rcp(float2 v) { return make_float2(__frcp_rn(v.x), __frcp_rn(v.y)); }
+    static __device__ __forceinline__ float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
 };
 
-// One pair of opposite directions with c.u = c: even part se = base +
-// 4.5 rho c^2, odd part so = 3 rho c; vp, vm the relaxed populations.
-template <typename V>
-__device__ __forceinline__ void relax_pair(V c, V ow, V omc, V r45, V r3, V base, V gp, V gm, V &vp, V &vm)
+
+// Lattice constants of the momentum-exact form, in the compute type T:
+// w0 = 4/9, w1 = 1/9, w5 = 1/36, and the odd-part weights 3 w1 = A1 and
+// 3 w5 = A5 chosen so that 2 A1 + 4 A5 = 1 holds exactly in T (the D2Q9
+// identity sum_i w_i c_ix c_ix = theta0 = 1/3, times 3).  With rounded 1/3 and
+// 1/12 the identity is off by a few units in the last place, and every
+// collision of a uniform-flow region then makes or destroys the same small
+// momentum at every node, a coherent drift of the whole flow.
+template <typename T> struct Lat {
+    static constexpr T W0 = T(4) / T(9), W1 = T(1) / T(9), W5 = T(1) / T(36);
+    static constexpr T A1 = T(1) / T(3);
+    static constexpr T A5 = (T(1) - T(2) * A1) * T(0.25);  // exact: 1 - 2 A1 and / 4 round nothing
+};
+
+// One pair of opposite directions: cj = c.j and cu = c.u of the direction
+// with the + sign.  The equilibrium deviations are
+//   eq+- = w (base + 4.5 (c.j)(c.u)) +- A (c.j)
+// (second order in u, theta0 = 1/3, rho u = j), and the relaxation is
+// ft = g + omega (eq - g), so that the old value enters with weight exactly
+// one.  eq - g is formed as w (...) + (+-A (c.j) - g): the large odd part and
+// the old value meet inside one fma, whose small result rounds far below the
+// storage precision, and the even part joins it in a second fma, so that the
+// only rounding at the size of g is the last.
+template <typename V, typename T>
+__device__ __forceinline__ void relax_pair_j(V cj, V cu, V w, V A, V om, V base, V gp, V gm, V &vp, V &vm)
 {
     using O = Arith<V>;
-    const V se = O::fma(O::mul(r45, c), c, base), so = O::mul(r3, c);
-    vp = O::fma(ow, O::add(se, so), O::mul(omc, gp));
-    vm = O::fma(ow, O::sub(se, so), O::mul(omc, gm));
+    const V se = O::fma(O::mul(cj, O::splat(T(4.5))), cu, base);
+    const V dp = O::fma(w, se, O::fma(A, cj, O::neg(gp)));
+    const V dm = O::fma(w, se, O::fma(O::neg(A), cj, O::neg(gm)));
+    vp = O::fma(om, dp, gp);
+    vm = O::fma(om, dm, gm);
 }
 
 // The collision of one node (V = T) or of two (V = float2, T = float); T is
@@ -86,28 +120,27 @@ template <typename V, typename T, bool DEV, bool FORCE>
 __device__ __forceinline__ void collide_core(const StepArgs &a, const V (&g)[9], V (&v)[9], V &rho)
 {
     using O = Arith<V>;
-    // uniform constants 1 - omega and omega w_i, computed once per launch
-    const V omc = O::splat(param<T>(a.omc, a.omc_f));
-    const V ow0 = O::splat(param<T>(a.ow[0], a.ow_f[0])), ow1 = O::splat(param<T>(a.ow[1], a.ow_f[1]));
-    const V ow5 = O::splat(param<T>(a.ow[2], a.ow_f[2]));
+    using L = Lat<T>;
+    const V om = O::splat(param<T>(a.omega, a.omega_f));
     const V jx = O::add(O::add(O::sub(g[1], g[3]), O::sub(g[5], g[6])), O::sub(g[8], g[7]));
     const V jy = O::sub(O::add(O::sub(g[2], g[4]), O::add(g[5], g[6])), O::add(g[7], g[8]));
+    const V jpd = O::add(jx, jy), jmd = O::sub(jy, jx);
     const V drho = O::add(O::add(O::add(O::add(g[0], g[1]), O::add(g[2], g[3])),
                                  O::add(O::add(g[4], g[5]), O::add(g[6], g[7]))),
                           g[8]);
     rho = DEV ? O::add(O::splat(param<T>(a.rho0, a.rho0_f)), drho) : drho;
     const V inv = O::rcp(rho);
     const V ux = O::mul(jx, inv), uy = O::mul(jy, inv);
-    const V usq = O::fma(ux, ux, O::mul(uy, uy));
-    const V base = O::fma(O::mul(rho, usq), O::splat(T(-1.5)), drho);
-    const V r45 = O::mul(rho, O::splat(T(4.5))), r3 = O::mul(rho, O::splat(T(3)));
-    v[0] = O::fma(ow0, base, O::mul(omc, g[0]));
-    // directions 1 (+x) and 3 (-x): c.u = ux; 2 (+y) and 4 (-y): c.u = uy;
-    // 5 (+x+y) and 7 (-x-y): ux + uy; 6 (-x+y) and 8 (+x-y): uy - ux
-    relax_pair<V>(ux, ow1, omc, r45, r3, base, g[1], g[3], v[1], v[3]);
-    relax_pair<V>(uy, ow1, omc, r45, r3, base, g[2], g[4], v[2], v[4]);
-    relax_pair<V>(O::add(ux, uy), ow5, omc, r45, r3, base, g[5], g[7], v[5], v[7]);
-    relax_pair<V>(O::sub(uy, ux), ow5, omc, r45, r3, base, g[6], g[8], v[6], v[8]);
+    // base = drho - 1.5 rho u^2 = drho - 1.5 j.u
+    const V base = O::fma(O::fma(jx, ux, O::mul(jy, uy)), O::splat(T(-1.5)), drho);
+    v[0] = O::fma(om, O::fma(O::splat(L::W0), base, O::neg(g[0])), g[0]);
+    const V w1 = O::splat(L::W1), w5 = O::splat(L::W5), a1 = O::splat(L::A1), a5 = O::splat(L::A5);
+    // directions 1 (+x) and 3 (-x); 2 (+y) and 4 (-y); 5 (+x+y) and 7 (-x-y);
+    // 6 (-x+y) and 8 (+x-y)
+    relax_pair_j<V, T>(jx, ux, w1, a1, om, base, g[1], g[3], v[1], v[3]);
+    relax_pair_j<V, T>(jy, uy, w1, a1, om, base, g[2], g[4], v[2], v[4]);
+    relax_pair_j<V, T>(jpd, O::add(ux, uy), w5, a5, om, base, g[5], g[7], v[5], v[7]);
+    relax_pair_j<V, T>(jmd, O::sub(uy, ux), w5, a5, om, base, g[6], g[8], v[6], v[8]);
     if constexpr (FORCE) {
         const T gx = param<T>(a.gx, a.gx_f), gy = param<T>(a.gy, a.gy_f);
 #pragma unroll

@@ -32,7 +32,9 @@ namespace gblbm {
 
 // Collide-stream tiles: 128 nodes along x by tile_rows(storage) rows.
 constexpr int TILE_X = 128;
-constexpr unsigned int WAIT_LIMIT = 1u << 22;  // bound on every mbarrier wait loop
+constexpr unsigned int WAIT_LIMIT = 1u << 22;  // default bound on every pipeline mbarrier wait
+// bound on each wait for copies already in flight after a pipeline wait gave up
+constexpr unsigned int DRAIN_LIMIT = 1u << 26;
 constexpr int PITCH_ALIGN = 64;
 constexpr int LINK_THREADS = 128;
 // Threads of the batched link kernel's one CTA per domain (a tuning knob):
@@ -141,35 +143,18 @@ struct StepArgs {
     int tile_off_x, tile_off_y;  // added to blockIdx (momentum-only pass)
     double omega, rho0, gx, gy;
     float omega_f, rho0_f, gx_f, gy_f;  // the same in FP32 (no FP64 conversions in FP32 kernels)
-    double omc, ow[3];       // 1 - omega and omega w_i for w = 4/9, 1/9, 1/36 (set_relaxation)
-    float omc_f, ow_f[3];    // the same rounded to FP32
     int cv[4];               // inclusive control-volume box
     int cvt[4];              // inclusive tile rectangle holding the box and its halo
     int use_bulk;            // staged (TMA) kernel allowed (channel set-up, pulled state)
     int sm_count;            // persistent grid size of the staged kernel
     int pf_rows;             // L2 prefetch distance of the direct kernel in tile rows (0: off)
+    unsigned int wait_limit; // polls of each pipeline wait of the staged kernel (WAIT_LIMIT)
 };
 
-// The relaxation constants of a StepArgs, from omega: the FP64 set in FP64
-// and the FP32 set in FP32 from the rounded omega, each in a fixed order, so
-// host and device give the same bits.  A kernel fills in only the set its
-// storage computes with (the FP32 kernels do no FP64 arithmetic for it).
-__host__ __device__ inline void set_relaxation_f64(StepArgs &a, double omega)
-{
-    a.omega = omega;
-    a.omc = 1.0 - omega;
-    a.ow[0] = omega * (4.0 / 9.0);
-    a.ow[1] = omega * (1.0 / 9.0);
-    a.ow[2] = omega * (1.0 / 36.0);
-}
-__host__ __device__ inline void set_relaxation_f32(StepArgs &a, float omega)
-{
-    a.omega_f = omega;
-    a.omc_f = 1.0f - omega;
-    a.ow_f[0] = omega * (4.0f / 9.0f);
-    a.ow_f[1] = omega * (1.0f / 9.0f);
-    a.ow_f[2] = omega * (1.0f / 36.0f);
-}
+// The relaxation rate of a StepArgs: the FP64 value and its FP32 rounding (a
+// kernel reads only the one its storage computes with).
+__host__ __device__ inline void set_relaxation_f64(StepArgs &a, double omega) { a.omega = omega; }
+__host__ __device__ inline void set_relaxation_f32(StepArgs &a, float omega) { a.omega_f = omega; }
 __host__ inline void set_relaxation(StepArgs &a, double omega)
 {
     set_relaxation_f64(a, omega);
@@ -247,16 +232,20 @@ cudaError_t launch_surface_pressure(int storage, const void *pop, const uint16_t
                                     long long count, long long plane, int nx, int ny, int pitch, int periodic,
                                     int precollision, double rho0, double p_inf, double q, double *cp,
                                     cudaStream_t st);
+// Drag and lift coefficients of a window of a force series (lbm_coeff.cu):
+// out[0..3] = mean C_d, mean C_l, std C_d, std C_l; with per_step, C_d and C_l
+// of every step follow ([count] each).  norm = 2 / (rho0 U^2 L).
+cudaError_t launch_coefficients(const double *series, long long row_stride, int col, long long first,
+                                long long count, int wrap, double norm, double *out, bool per_step,
+                                cudaStream_t st);
 cudaError_t launch_scatter_pop(int storage, void *pop, const uint16_t *nbits, long long plane,
                                int nx, int ny, int pitch, double rho0, int plane_i,
                                const double *in, cudaStream_t st);
 
-// discrete adjoint (lbm_adjoint.cu)
-cudaError_t launch_precollision(int storage, const void *src, const uint16_t *nbits, long long plane,
-                                int nx, int ny, int pitch, int precollision, void *out,
-                                cudaStream_t st);
+// discrete adjoint (lbm_adjoint.cu): one backward step; src holds ft(t-1) in
+// the storage type (f(t) itself when precollision), pulled inside the kernel
 int adjoint_blocks(int nx, int ny);
-cudaError_t launch_adjoint_step(int storage, const void *fpre, const void *lam_next, void *lam,
+cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, const void *lam_next, void *lam,
                                 const uint16_t *nbits, const double *u_row, double *du_acc,
                                 double *dw_acc, long long plane, int nx, int ny, int pitch,
                                 int in_window, double omega, double rho0, double obj_x,

@@ -7,7 +7,6 @@
 // array instead of memory from an allocator, and the neighbour bits are taken
 // from the mask on the fly.
 #include <cstdio>
-#include <mutex>
 
 #include "lbm_internal.cuh"
 
@@ -95,9 +94,6 @@ k_noalloc_scatter(const uint8_t *__restrict__ mask, int nx, int ny, int periodic
         }
 }
 
-std::mutex g_mu;
-int *g_addr[64];  // device address of g_noalloc_scratch, per device ordinal
-
 }  // namespace
 
 }  // namespace gblbm
@@ -121,28 +117,27 @@ extern "C" lbm_status lbm_links_noalloc(const uint8_t *d_mask, int nx, int ny, i
         set_thread_error(buf);
         return LBM_EINVAL;
     }
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
-        set_thread_error("lbm_links_noalloc: no current CUDA device");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // The call reads its result back and waits for the stream, so it cannot
+    // be recorded into a graph: refuse a stream that is being captured.
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap_status);
+    if (e != cudaSuccess || cap_status != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        set_thread_error("lbm_links_noalloc: the stream is being captured (or is invalid); "
+                         "this call is synchronous and cannot be captured");
+        return LBM_EINVAL;
+    }
+    // Host code sees only a stand-in for the static array.  Its device address
+    // is asked for on every call, with the caller's device current, so that a
+    // reset device or another context never leaves a stale address behind.
+    int *scratch = nullptr;
+    e = cudaGetSymbolAddress((void **)&scratch, g_noalloc_scratch);
+    if (e != cudaSuccess || !scratch) {
+        cudaGetLastError();
+        set_thread_error("lbm_links_noalloc: cudaGetSymbolAddress failed (no usable CUDA device?)");
         return LBM_ECUDA;
     }
-    int *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {
-            // host code sees only a stand-in for the static array: ask the runtime
-            // for its address on this device once, with the device current
-            e = cudaGetSymbolAddress((void **)&g_addr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_addr[dev] = nullptr;
-                set_thread_error("lbm_links_noalloc: cudaGetSymbolAddress failed");
-                return LBM_ECUDA;
-            }
-        }
-        scratch = g_addr[dev];
-    }
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const int nblocks = (int)((N + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK);
     long long *total_d = (long long *)(scratch + NOALLOC_MAX_BLOCKS);
     k_noalloc_count<<<nblocks, NOALLOC_BLOCK, 0, st>>>(d_mask, nx, ny, periodic_x, scratch);

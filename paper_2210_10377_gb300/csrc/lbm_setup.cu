@@ -291,26 +291,110 @@ __device__ __forceinline__ double feq_row(int i, double rho0, double u)
     return wgt<double>(i) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u * u);
 }
 
+// Storage values next to v: the nearest (lo) and its neighbour on the other
+// side of v (hi; equal to lo when v is representable).
+__device__ void bracket(double v, float &lo, float &hi)
+{
+    lo = (float)v;
+    if ((double)lo == v) {
+        hi = lo;
+        return;
+    }
+    hi = nextafterf(lo, (double)lo < v ? INFINITY : -INFINITY);
+}
+__device__ void bracket(double v, __half &lo, __half &hi)
+{
+    lo = __double2half(v);
+    const double l = (double)__half2float(lo);
+    if (l == v) {
+        hi = lo;
+        return;
+    }
+    // one step along the 16-bit pattern towards v
+    unsigned short b = __half_as_ushort(lo);
+    const bool up = l < v;
+    if ((b & 0x7fff) == 0)
+        b = up ? 0x0001 : 0x8001;
+    else if (((b & 0x8000) == 0) == up)
+        b = (unsigned short)(b + 1);
+    else
+        b = (unsigned short)(b - 1);
+    hi = __ushort_as_half(b);
+}
+__device__ double as_double(float v) { return (double)v; }
+__device__ double as_double(__half v) { return (double)__half2float(v); }
+
+// The inlet state of each row, feq(rho0, (u_in(y), 0)) (less w_i rho0 for
+// deviation storage), rounded to the storage type.  Rounding each value to
+// nearest by itself changes the row's density and momentum by up to a few
+// half-units in the last place of the storage type (for FP16 deviations about
+// 2e-4 of rho0 u_in in the momentum, which the whole flow then carries).  So
+// each value takes the nearer or the farther of its two bracketing storage
+// values, whichever of the 2^9 choices keeps the mass and both momentum
+// components closest to the exact ones (sum of squared errors; ties go to the
+// choice nearer element by element).  FP64 storage stores the values as they are.
+template <int S>
+__global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int ny,
+                             typename Traits<S>::store_t *__restrict__ inlet)
+{
+    using ST = typename Traits<S>::store_t;
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= ny) return;
+    const double u = u_row[y];
+    double v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        v[i] = feq_row(i, rho0, u);
+        if (Traits<S>::dev) v[i] -= wgt<double>(i) * rho0;
+    }
+    if constexpr (S == LBM_F64) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) inlet[i * ny + y] = v[i];
+    } else {
+        ST lo[9], hi[9];
+        double dl[9], dh[9];
+        for (int i = 0; i < 9; ++i) {
+            bracket(v[i], lo[i], hi[i]);
+            dl[i] = as_double(lo[i]) - v[i];
+            dh[i] = as_double(hi[i]) - v[i];
+        }
+        unsigned best = 0;
+        double best_e = INFINITY, best_a = INFINITY;
+        for (unsigned c = 0; c < 512u; ++c) {
+            double dr = 0.0, jx = 0.0, jy = 0.0, ab = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                const double d = (c >> i) & 1u ? dh[i] : dl[i];
+                dr += d;
+                jx += cx(i) * d;
+                jy += cy(i) * d;
+                ab += fabs(d);
+            }
+            const double e = dr * dr + jx * jx + jy * jy;
+            if (e < best_e || (e == best_e && ab < best_a)) {
+                best_e = e;
+                best_a = ab;
+                best = c;
+            }
+        }
+        for (int i = 0; i < 9; ++i) inlet[i * ny + y] = (best >> i) & 1u ? hi[i] : lo[i];
+    }
+}
+
+// Initial state: every fluid node of row y holds the row's inlet state.
 template <int S>
 __global__ void k_init(typename Traits<S>::store_t *__restrict__ pop, long long plane,
                        const uint8_t *__restrict__ mask, int nx, int ny, int pitch,
-                       const double *__restrict__ u_row, double rho0,
-                       typename Traits<S>::store_t *__restrict__ inlet)
+                       const typename Traits<S>::store_t *__restrict__ inlet)
 {
     using ST = typename Traits<S>::store_t;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     if (x >= nx) return;
     bool solid = mask[(long long)y * nx + x] != 0;
-    double u = u_row[y];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        double v = feq_row(i, rho0, u);
-        if (Traits<S>::dev) v -= wgt<double>(i) * rho0;
-        ST s = to_store<ST>((typename Traits<S>::comp_t)v);
-        pop[i * plane + (long long)y * pitch + x] = solid ? to_store<ST>((typename Traits<S>::comp_t)0) : s;
-        if (x == 0) inlet[i * ny + y] = s;
-    }
+    for (int i = 0; i < 9; ++i)
+        pop[i * plane + (long long)y * pitch + x] =
+            solid ? to_store<ST>((typename Traits<S>::comp_t)0) : inlet[i * ny + y];
 }
 
 cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *mask, int nx,
@@ -318,22 +402,24 @@ cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *
                         cudaStream_t st)
 {
     dim3 grid((nx + 255) / 256, ny);
+    const int rb = (ny + 127) / 128;
     switch (storage) {
     case LBM_F64:
-        k_init<LBM_F64><<<grid, 256, 0, st>>>((double *)pop, plane, mask, nx, ny, pitch, u_row,
-                                               rho0, (double *)inlet);
+        k_inlet_rows<LBM_F64><<<rb, 128, 0, st>>>(u_row, rho0, ny, (double *)inlet);
+        k_init<LBM_F64><<<grid, 256, 0, st>>>((double *)pop, plane, mask, nx, ny, pitch, (const double *)inlet);
         break;
     case LBM_F32:
-        k_init<LBM_F32><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch, u_row,
-                                               rho0, (float *)inlet);
+        k_inlet_rows<LBM_F32><<<rb, 128, 0, st>>>(u_row, rho0, ny, (float *)inlet);
+        k_init<LBM_F32><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch, (const float *)inlet);
         break;
     case LBM_F32_DEV:
-        k_init<LBM_F32_DEV><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch,
-                                                   u_row, rho0, (float *)inlet);
+        k_inlet_rows<LBM_F32_DEV><<<rb, 128, 0, st>>>(u_row, rho0, ny, (float *)inlet);
+        k_init<LBM_F32_DEV><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch, (const float *)inlet);
         break;
     default:
+        k_inlet_rows<LBM_F16_DEV><<<rb, 128, 0, st>>>(u_row, rho0, ny, (__half *)inlet);
         k_init<LBM_F16_DEV><<<grid, 256, 0, st>>>((__half *)pop, plane, mask, nx, ny, pitch,
-                                                   u_row, rho0, (__half *)inlet);
+                                                   (const __half *)inlet);
         break;
     }
     return cudaGetLastError();

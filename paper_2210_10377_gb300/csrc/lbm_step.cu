@@ -135,9 +135,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 // Bounded wait; false when the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// At most `limit` polls; false if the phase did not complete within them.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
 {
-    for (uint32_t k = 0; k < WAIT_LIMIT; ++k)
+    for (uint32_t k = 0; k < limit; ++k)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -289,12 +290,16 @@ __global__ void __launch_bounds__(TmaCfg<S>::THREADS, GBLBM_TMA_MINB)
         // one thread waits (bounded) for the stage; the barrier hands the data
         // and the outcome to the whole CTA, so every thread takes the same path
         bool ok = true;
-        if (threadIdx.x == 0) ok = tma::mbar_wait(&bar[s], parity);
+        if (threadIdx.x == 0) ok = tma::mbar_wait(&bar[s], parity, a.wait_limit);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicOr(a.status, 2);
-                for (int j = k + 1; j < count && j < k + C::NS; ++j)
-                    tma::mbar_wait(&bar[j % C::NS], (uint32_t)(j / C::NS) & 1u);
+                // The copies issued so far fill the stages of tiles k .. k+NS-1,
+                // stage k's (whose wait just gave up) included.  Wait for every one
+                // of them, each within its own generous bound, so that no bulk copy
+                // is still writing this CTA's shared memory when the CTA exits.
+                for (int j = k; j < count && j < k + C::NS; ++j)
+                    tma::mbar_wait(&bar[j % C::NS], (uint32_t)(j / C::NS) & 1u, DRAIN_LIMIT);
             }
             return;
         }

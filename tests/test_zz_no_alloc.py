@@ -6,15 +6,19 @@ fixed device-memory budget or its own pool, a plug-in whose host forbids
 cudaMalloc, or a latency-bound loop that cannot absorb the synchronisation
 cudaMalloc/cudaFree may trigger.  Such a caller hands in device buffers it
 already owns; this entry point works in a fixed static scratch array instead.
-Here the caller's buffers come from torch, and the result is checked against
-the handle-based lbm_links() entry point, twice in a row, so that the second
-call also shows that scratch contents left by the first do not leak through.
+Here the caller's buffers come from torch.  The result is checked against the
+oracle's link list (the definition of a link: a fluid node next to a solid
+one, Section II) and against the handle-based lbm_links() entry point, twice in
+a row, so that the second call also shows that scratch contents left by the
+first do not leak through.  A short output buffer gets the first links and the
+full count, and nothing past its end is written.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2210_10377_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -68,6 +72,50 @@ def test_noalloc_links_match_lbm_links_twice(env):
         want = handle_links(binding, mask, periodic)
         assert got.size > 0
         assert np.array_equal(got, want)
+        assert np.array_equal(got, oracle.links(mask, periodic_x=periodic))
+
+
+def test_noalloc_short_buffer_gets_prefix_and_full_count(env):
+    torch, binding, L = env
+    stream = torch.cuda.Stream()
+    mask = inputs.random_blobs_mask(257, 45, 12, seed=19, margin_x=2)
+    want = oracle.links(mask)
+    cap = want.size // 2
+    assert cap > 0
+    d_mask = torch.from_numpy(mask).to("cuda")
+    d_links = torch.full((want.size + 64,), -1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        d_links.fill_(-1)
+        count = C.c_long(-1)
+        torch.cuda.synchronize()
+        rc = L.lbm_links_noalloc(d_mask.data_ptr(), mask.shape[1], mask.shape[0], 0,
+                                 d_links.data_ptr(), cap, C.byref(count), stream.cuda_stream)
+        assert rc == 0, L.lbm_last_error(None)
+        assert count.value == want.size
+        got = d_links.cpu().numpy()
+        assert np.array_equal(got[:cap], want[:cap])
+        assert (got[cap:] == -1).all()
+
+
+def test_noalloc_refuses_a_capturing_stream(env):
+    torch, binding, L = env
+    mask = inputs.random_blobs_mask(64, 16, 3, seed=5, margin_x=2)
+    d_mask = torch.from_numpy(mask).to("cuda")
+    d_links = torch.full((256,), -1, dtype=torch.int32, device="cuda")
+    x = torch.zeros(4, device="cuda")
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    count = C.c_long(-3)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=stream):
+        x.add_(1.0)
+        rc = L.lbm_links_noalloc(d_mask.data_ptr(), mask.shape[1], mask.shape[0], 0,
+                                 d_links.data_ptr(), 256, C.byref(count), stream.cuda_stream)
+    assert rc == 1 and b"captured" in L.lbm_last_error(None)
+    assert count.value == -3
+    # the refused call queued nothing; the next plain call still works
+    got = noalloc_links(torch, L, mask, False, torch.cuda.Stream())
+    assert np.array_equal(got, oracle.links(mask))
 
 
 def test_noalloc_links_same_call_twice_and_full_size(env):
@@ -79,6 +127,7 @@ def test_noalloc_links_same_call_twice_and_full_size(env):
     a = noalloc_links(torch, L, mask, False, stream)
     b = noalloc_links(torch, L, mask, False, stream)
     assert np.array_equal(a, want) and np.array_equal(b, want)
+    assert np.array_equal(a, oracle.links(mask))
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(env):
