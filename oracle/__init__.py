@@ -63,8 +63,17 @@ def lib():
         L.oracle_adjoint.argtypes = [up, C.c_int, C.c_int, C.c_double, dp, dp, C.c_int, C.c_int,
                                      C.c_double, C.c_double, dp, dp, dp, dp]
         L.oracle_adjoint.restype = C.c_int
+        L.oracle_set_threads.argtypes = [C.c_int]
+        L.oracle_set_threads.restype = C.c_int
+        L.oracle_set_threads(1)
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Host threads for the oracle's node loops; returns the count in use.
+    The results are the same for any count."""
+    return lib().oracle_set_threads(int(n))
 
 
 def _dp(a):

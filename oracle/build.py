@@ -1,7 +1,8 @@
 """Compile the FP64 CPU oracle (test infrastructure) into oracle/_build/.
 
 The oracle is plain C, compiled without floating-point contraction so that the
-NACA mask predicate is evaluated with separately rounded operations.
+NACA mask predicate is evaluated with separately rounded operations, and with
+OpenMP for its node loops (one thread unless oracle.set_threads says otherwise).
 """
 import os
 import subprocess
@@ -19,7 +20,7 @@ def build_oracle(force: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fopenmp",
            "-shared", SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)

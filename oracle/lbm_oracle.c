@@ -33,6 +33,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -382,6 +385,9 @@ static void step_once(oracle_sim *s)
      *     ft = f + 2 beta (feq(rho, u) - f), 2 beta = 1/tau.
      *     A uniform body force g (used only by test set-ups) adds 3 w_i c_i.g.
      *     Inlet column (channel set-up): ft = feq(rho0, (u_in(y), 0)). */
+    /* Nodes are independent: the loop may run on several threads (the values
+     * do not depend on how it is split). */
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (s->mask[n]) continue;
         int x = (int)(n % nx), y = (int)(n / nx);
@@ -484,6 +490,10 @@ static void step_once(oracle_sim *s)
     /* (5) Advection f(x + c_i, t+1) = ft_i(x, t), with halfway bounce-back
      *     f_opp(x_f, t+1) = ft_i(x_f, t) when x_f + c_i is solid. */
     memset(fn, 0, sizeof(double) * 9 * N);
+    /* Every target population is written by exactly one source node (a node
+     * next to a solid is never the target of a push from it), so the loop may
+     * run on several threads. */
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (s->mask[n]) continue;
         int x = (int)(n % nx), y = (int)(n / nx);
@@ -538,6 +548,20 @@ static void step_once(oracle_sim *s)
     s->f = fn;
     s->fn = f;
     s->t += 1;
+}
+
+/* Host threads for the node loops of oracle_step (1 by default); returns the
+ * count in use.  The results do not depend on it: the force, flux and momentum
+ * sums always run on one thread in their fixed order. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Advance n steps; returns 0, or -1 on allocation failure. */

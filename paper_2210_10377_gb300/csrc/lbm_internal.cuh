@@ -250,6 +250,6 @@ cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, 
                                 double *dw_acc, long long plane, int nx, int ny, int pitch,
                                 int in_window, double omega, double rho0, double obj_x,
                                 double obj_y, cudaStream_t st);
-cudaError_t launch_sum_serial(const double *v, long long n, double *out, cudaStream_t st);
+cudaError_t launch_sum_fixed(const double *v, long long n, double *out, cudaStream_t st);
 
 }  // namespace gblbm

@@ -394,3 +394,22 @@ def test_checkpoint_resume_bitwise(oracle_mod):
     s3.set_populations(f)
     s3.step(20)
     np.testing.assert_array_equal(s1.populations(), s3.populations())
+
+
+def test_threads_do_not_change_the_results():
+    # the node loops may run on several host threads; every sum keeps its
+    # single-threaded order, so the trajectory and every force are bitwise equal
+    import oracle
+    m = inputs.random_blobs_mask(97, 41, 8, seed=12, margin_x=3)
+    f0 = inputs.random_populations(97, 41, seed=13, lo=0.05, hi=0.12) * (1 - m)[None]
+    runs = []
+    for th in (1, 4):
+        oracle.set_threads(th)
+        s = oracle.Sim(m, 0.6, inputs.random_inlet(41, seed=14))
+        s.set_populations(f0)
+        s.step(25)
+        runs.append((s.populations(), [s.force_series(k) for k in range(5)]))
+    oracle.set_threads(1)
+    assert np.array_equal(runs[0][0], runs[1][0])
+    for a, b in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
