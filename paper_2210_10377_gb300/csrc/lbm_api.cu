@@ -26,7 +26,11 @@ thread_local std::string g_thread_err;
 // concurrently with the collide-stream kernel of step t+1 (writing b(t+1));
 // the collide-stream kernel of step t+2 waits for it before overwriting b(t-1).
 constexpr int NBUF = 3;
-constexpr int GRAPH_STEPS = 15;  // steps per captured graph (a multiple of NBUF)
+#ifndef GBLBM_GRAPH_STEPS
+#define GBLBM_GRAPH_STEPS 15
+#endif
+constexpr int GRAPH_STEPS = GBLBM_GRAPH_STEPS;  // steps per captured graph (a multiple of NBUF)
+static_assert(GRAPH_STEPS % NBUF == 0 && GRAPH_STEPS >= NBUF, "GRAPH_STEPS: a multiple of NBUF");
 constexpr int TIMING_BATCH = 64;
 
 }  // namespace
@@ -57,6 +61,11 @@ struct lbm_ctx {
     cudaStream_t side = nullptr; // link kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_read[NBUF] = {nullptr, nullptr, nullptr};
     bool ev_live[NBUF] = {false, false, false};
+    // The step whose collide-stream kernel is queued and whose link kernel is
+    // not yet (lead_src < 0: none): it goes out beside the next step's
+    // collide-stream kernel, or when the queue ends.
+    int lead_src = -1, lead_pre = 0;
+    int link_prio = 0;           // launch priority of the link kernels (the device's highest)
     uint8_t *mask_d = nullptr;
     uint16_t *nbits = nullptr;
     uint8_t *tile_flag = nullptr;
@@ -83,7 +92,8 @@ struct lbm_ctx {
     int precollision = 1;
     long long carry_from = 0;    // first step of the current DRTT chain
     long long drtt_ready = 0;    // DRTT(s) is final for s < drtt_ready
-    cudaGraphExec_t graph[NBUF][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    // [start buffer][GRAPH_STEPS or NBUF steps][opens with the previous step's link kernel]
+    cudaGraphExec_t graph[NBUF][2][2] = {};
     bool timing = false;
     std::vector<cudaEvent_t> events;
     double kt_ms[2] = {0, 0};
@@ -182,6 +192,7 @@ bool encode_tensor_map(CUtensorMap *m, int storage, void *base, int pitch, int n
 }
 
 int next_buf(int b) { return b + 1 == NBUF ? 0 : b + 1; }
+int prev_buf(int b) { return b == 0 ? NBUF - 1 : b - 1; }
 
 StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
 {
@@ -253,36 +264,29 @@ LinkArgs link_args(lbm_ctx *h, int src, int dst, int precollision, int drtt_only
     return a;
 }
 
-// One step t -> t+1 from buffer src into next_buf(src): the collide-stream
-// kernel on the handle's stream, then the link kernel.  Normally the link
-// kernel goes to the side stream (forked after the collide-stream kernel) and
-// the next-but-one collide-stream kernel waits for it; with timing events
-// (ev != NULL) both run in order on the handle's stream, each between events.
-cudaError_t launch_one_step(lbm_ctx *h, int src, int precollision, cudaEvent_t *ev)
+// The link kernel of the step that read buffer src, on the side stream,
+// forked after everything queued so far on the handle's stream (that step's
+// collide-stream kernel included); the collide-stream kernel that overwrites
+// src next waits for it (ev_read).
+cudaError_t launch_link_side(lbm_ctx *h, int src, int precollision)
 {
-    const int dst = next_buf(src);
-    cudaError_t e = cudaSuccess;
-    if (!ev && h->ev_live[dst]) e = cudaStreamWaitEvent(h->stream, h->ev_read[dst], 0);
-    if (e != cudaSuccess) return e;
-    StepArgs sa = step_args(h, src, dst, precollision);
-    if (ev) cudaEventRecord(ev[0], h->stream);
-    e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false,
-                              h->tmap_ok ? (const void *)&h->tmap[src] : nullptr, h->stream);
-    if (e != cudaSuccess) return e;
-    LinkArgs la = link_args(h, src, dst, precollision, 0);
-    if (ev) {
-        cudaEventRecord(ev[1], h->stream);
-        e = launch_link_force(h->storage, la, h->stream);
-        cudaEventRecord(ev[2], h->stream);
-    } else {
-        e = cudaEventRecord(h->ev_fork, h->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-        if (e == cudaSuccess) e = launch_link_force(h->storage, la, h->side);
-        if (e == cudaSuccess) e = cudaEventRecord(h->ev_read[src], h->side);
-        h->ev_live[src] = true;
-    }
-    h->launches += 2;
+    LinkArgs la = link_args(h, src, next_buf(src), precollision, 0);
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_link_force(h->storage, la, h->side, h->link_prio);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_read[src], h->side);
+    h->ev_live[src] = true;
+    h->launches += 1;
     return e;
+}
+
+// Launches the held link kernel, if any.
+cudaError_t flush_link(lbm_ctx *h)
+{
+    if (h->lead_src < 0) return cudaSuccess;
+    const int src = h->lead_src;
+    h->lead_src = -1;
+    return launch_link_side(h, src, h->lead_pre);
 }
 
 // Join the side stream back into the handle's stream.
@@ -294,21 +298,70 @@ cudaError_t join_side(lbm_ctx *h)
     return e;
 }
 
+// One step t -> t+1 from buffer src into next_buf(src).  Normally the
+// collide-stream kernel goes to the handle's stream and its link kernel is
+// held (lead_src): it is launched on the side stream beside the next step's
+// collide-stream kernel, so that no link kernel waits alone between two
+// steps, not even across the end of a captured graph.  The collide-stream
+// kernel first waits for the link kernel of step t-2, which read the buffer
+// it overwrites.  With timing events (ev != NULL) both kernels run in order
+// on the handle's stream, each between events.
+cudaError_t launch_one_step(lbm_ctx *h, int src, int precollision, cudaEvent_t *ev)
+{
+    const int dst = next_buf(src);
+    cudaError_t e = cudaSuccess;
+    StepArgs sa = step_args(h, src, dst, precollision);
+    if (ev) {
+        if (h->lead_src >= 0) {
+            e = flush_link(h);
+            if (e == cudaSuccess) e = join_side(h);
+            if (e != cudaSuccess) return e;
+        }
+        cudaEventRecord(ev[0], h->stream);
+        e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false,
+                                  h->tmap_ok ? (const void *)&h->tmap[src] : nullptr, h->stream);
+        if (e != cudaSuccess) return e;
+        LinkArgs la = link_args(h, src, dst, precollision, 0);
+        cudaEventRecord(ev[1], h->stream);
+        e = launch_link_force(h->storage, la, h->stream);
+        cudaEventRecord(ev[2], h->stream);
+        h->launches += 2;
+        return e;
+    }
+    e = flush_link(h);
+    if (e == cudaSuccess && h->ev_live[dst]) e = cudaStreamWaitEvent(h->stream, h->ev_read[dst], 0);
+    if (e != cudaSuccess) return e;
+    e = launch_collide_stream(h->storage, sa, h->tiles_x, h->tiles_y, false,
+                              h->tmap_ok ? (const void *)&h->tmap[src] : nullptr, h->stream);
+    h->lead_src = src;
+    h->lead_pre = precollision;
+    h->launches += 1;
+    return e;
+}
+
 void drop_graphs(lbm_ctx *h)
 {
     for (int p = 0; p < NBUF; ++p)
         for (int k = 0; k < 2; ++k)
-            if (h->graph[p][k]) {
-                cudaGraphExecDestroy(h->graph[p][k]);
-                h->graph[p][k] = nullptr;
-            }
+            for (int l = 0; l < 2; ++l)
+                if (h->graph[p][k][l]) {
+                    cudaGraphExecDestroy(h->graph[p][k][l]);
+                    h->graph[p][k][l] = nullptr;
+                }
 }
 
-lbm_status build_graph(lbm_ctx *h, int p, int k)
+// Captures GRAPH_STEPS (k = 0) or NBUF (k = 1) steps from buffer p.  lead = 1:
+// the graph opens with the held link kernel of the step before (which read
+// prev_buf(p)) beside its first collide-stream kernel.  Either way the graph
+// ends with its last step's link kernel held: the caller sets lead_src.
+lbm_status build_graph(lbm_ctx *h, int p, int k, int lead)
 {
     int steps = k == 0 ? GRAPH_STEPS : NBUF;
     cudaGraph_t g = nullptr;
     for (int b = 0; b < NBUF; ++b) h->ev_live[b] = false;
+    const int saved_src = h->lead_src, saved_pre = h->lead_pre;
+    h->lead_src = lead ? prev_buf(p) : -1;
+    h->lead_pre = 0;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t le = cudaSuccess;
     long long saved = h->launches;
@@ -319,13 +372,15 @@ lbm_status build_graph(lbm_ctx *h, int p, int k)
     }
     if (le == cudaSuccess) le = join_side(h);
     h->launches = saved;
+    h->lead_src = saved_src;
+    h->lead_pre = saved_pre;
     cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
     if (le != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return cuda_err(h, le, "capture step kernels");
     }
     if (ee != cudaSuccess) return cuda_err(h, ee, "end capture");
-    cudaError_t ie = cudaGraphInstantiate(&h->graph[p][k], g, 0);
+    cudaError_t ie = cudaGraphInstantiateWithFlags(&h->graph[p][k][lead], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) return cuda_err(h, ie, "instantiate graph");
     return LBM_OK;
@@ -502,7 +557,10 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
         h->own_stream = true;
     }
     {
-        cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        int least = 0, greatest = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        h->link_prio = greatest;
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
         for (int b = 0; b < NBUF && e == cudaSuccess; ++b)
@@ -579,6 +637,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     CKC(cudaMemsetAsync(h->step_ctr, 0, sizeof(long long), s), "memset");
     const int status0[2] = {0, INT_MAX};
     CKC(cudaMemcpyAsync(h->status, status0, sizeof(status0), cudaMemcpyHostToDevice, s), "H2D status");
+    h->status_armed = true;
     CKC(cudaMemcpyAsync(h->mask_d, mask, N, cudaMemcpyHostToDevice, s), "H2D mask");
     CKC(cudaMemcpyAsync(h->u_row, urow.data(), sizeof(double) * ny, cudaMemcpyHostToDevice, s), "H2D u_in");
     CKC(launch_node_bits(h->mask_d, h->nbits, nx, ny, h->pitch, periodic, s), "node bits");
@@ -661,7 +720,6 @@ lbm_status queue_steps(lbm_ctx *h, int n)
             if (!e) CK(h, cudaEventCreate(&e), "event create");
     }
     int nev = 0;
-    for (int b = 0; b < NBUF; ++b) h->ev_live[b] = false;
     while (n > 0) {
         if (h->precollision || h->timing || n < NBUF) {
             cudaEvent_t *ev = h->timing ? &h->events[3 * nev] : nullptr;
@@ -678,17 +736,24 @@ lbm_status queue_steps(lbm_ctx *h, int n)
         } else {
             int k = n >= GRAPH_STEPS ? 0 : 1;
             int steps = k == 0 ? GRAPH_STEPS : NBUF;
+            // a held link kernel of the step before opens the graph
+            const int lead = h->lead_src == prev_buf(h->cur) && !h->lead_pre ? 1 : 0;
+            if (!lead) CK(h, flush_link(h), "link launch");
+            // the graph's first steps overwrite buffers that launched link kernels read
             CK(h, join_side(h), "join");
-            if (!h->graph[h->cur][k]) {
-                st = build_graph(h, h->cur, k);
+            if (!h->graph[h->cur][k][lead]) {
+                st = build_graph(h, h->cur, k, lead);
                 if (st != LBM_OK) return st;
             }
-            CK(h, cudaGraphLaunch(h->graph[h->cur][k], h->stream), "graph launch");
-            h->launches += 2 * steps;
+            CK(h, cudaGraphLaunch(h->graph[h->cur][k][lead], h->stream), "graph launch");
+            h->lead_src = prev_buf(h->cur);  // steps is a multiple of NBUF
+            h->lead_pre = 0;
+            h->launches += 2 * steps - 1 + lead;  // the last link kernel is held
             h->t += steps;
             n -= steps;
         }
     }
+    CK(h, flush_link(h), "link launch");
     CK(h, join_side(h), "join");
     if (h->timing) {
         st = flush_timing(h, nev);
@@ -706,7 +771,11 @@ lbm_status settle(lbm_ctx *h)
     h->status_armed = false;
     CK(h, cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream),
        "D2H status");
+    // clear the words for the next queue here, so that its start waits on nothing
+    CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
+    CK(h, cudaMemsetAsync(h->status + 1, 0x7f, sizeof(int), h->stream), "status reset");
     CK(h, cudaStreamSynchronize(h->stream), "step sync");
+    h->status_armed = true;
     const int *status = h->status_host;
     if (h->t - 1 > h->carry_from) h->drtt_ready = h->t - 1 > h->drtt_ready ? h->t - 1 : h->drtt_ready;
     if (status[0] & 4)
@@ -823,10 +892,11 @@ lbm_status lbm_prepare(lbm_ctx *h, long n)
     if (st != LBM_OK) return st;
     for (int p = 0; p < NBUF; ++p)
         for (int k = 0; k < 2; ++k)
-            if (!h->graph[p][k]) {
-                st = build_graph(h, p, k);
-                if (st != LBM_OK) return st;
-            }
+            for (int l = 0; l < 2; ++l)
+                if (!h->graph[p][k][l]) {
+                    st = build_graph(h, p, k, l);
+                    if (st != LBM_OK) return st;
+                }
     return LBM_OK;
 }
 

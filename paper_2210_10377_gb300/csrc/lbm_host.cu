@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "gblbm.h"
 #include "lbm_host.h"
@@ -17,17 +18,39 @@ size_t storage_bytes(int storage)
     }
 }
 
+namespace {
+
+// Row-major indices of the solid (nonzero) mask bytes.  Masks are mostly
+// fluid, so eight bytes are tested at a time and zero words skipped.
+std::vector<long long> solid_nodes(const uint8_t *mask, int nx, int ny)
+{
+    std::vector<long long> out;
+    const size_t n = (size_t)nx * ny;
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t w;
+        memcpy(&w, mask + i, 8);
+        if (w == 0) continue;
+        for (size_t k = i; k < i + 8; ++k)
+            if (mask[k]) out.push_back((long long)k);
+    }
+    for (; i < n; ++i)
+        if (mask[i]) out.push_back((long long)i);
+    return out;
+}
+
+}  // namespace
+
 void auto_cv(const uint8_t *mask, int nx, int ny, int periodic, int *cv)
 {
     int xmin = nx, xmax = -1, ymin = ny, ymax = -1;
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x)
-            if (mask[(size_t)y * nx + x]) {
-                xmin = x < xmin ? x : xmin;
-                xmax = x > xmax ? x : xmax;
-                ymin = y < ymin ? y : ymin;
-                ymax = y > ymax ? y : ymax;
-            }
+    for (long long k : solid_nodes(mask, nx, ny)) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+        xmin = x < xmin ? x : xmin;
+        xmax = x > xmax ? x : xmax;
+        ymin = y < ymin ? y : ymin;
+        ymax = y > ymax ? y : ymax;
+    }
     if (xmax < 0) {
         cv[0] = periodic ? 0 : 1;
         cv[1] = periodic ? nx - 1 : nx - 2;
@@ -67,29 +90,33 @@ void base_sums(const uint8_t *mask, int nx, int ny, int periodic, const int *cv,
     const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     auto W = [](int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); };
     auto solid = [&](int x, int y) { return mask[(size_t)y * nx + x] != 0; };
+    // coordinates here are at most two nodes outside the grid
     auto wrap = [&](int &x, int &y) {
-        y = (y % ny + ny) % ny;
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
         if (x < 0 || x >= nx) {
             if (!periodic) return false;
-            x = (x % nx + nx) % nx;
+            x = x < 0 ? x + nx : x - nx;
         }
         return true;
     };
     double lb[2] = {0, 0};
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-            if (!solid(x, y)) continue;
-            for (int i = 1; i < 9; ++i) {  // fluid x_f = s - c_i with x_f + c_i = s
-                int xf = x - CX[i], yf = y - CY[i];
-                if (!wrap(xf, yf) || solid(xf, yf)) continue;
-                lb[0] += CX[i] * W(i);
-                lb[1] += CY[i] * W(i);
-            }
+    for (long long k : solid_nodes(mask, nx, ny)) {  // row-major, like a plain double loop
+        const int x = (int)(k % nx), y = (int)(k / nx);
+        for (int i = 1; i < 9; ++i) {  // fluid x_f = s - c_i with x_f + c_i = s
+            int xf = x - CX[i], yf = y - CY[i];
+            if (!wrap(xf, yf) || solid(xf, yf)) continue;
+            lb[0] += CX[i] * W(i);
+            lb[1] += CY[i] * W(i);
         }
+    }
     double fb[2] = {0, 0};
     auto inbox = [&](int x, int y) { return x >= cv[0] && x <= cv[1] && y >= cv[2] && y <= cv[3]; };
     for (int y = cv[2] - 1; y <= cv[3] + 1; ++y)
         for (int x = cv[0] - 1; x <= cv[1] + 1; ++x) {
+            if (y > cv[2] && y < cv[3] && x > cv[0] && x < cv[1]) {
+                x = cv[1] - 1;  // every neighbour of an interior node is inside: no crossing
+                continue;
+            }
             int xn = x, yn = y;
             if (!wrap(xn, yn)) continue;
             if (x != xn || y != yn) continue;  // each node once, in unwrapped position

@@ -221,7 +221,9 @@ size_t tma_stage_bytes(int storage);
 // type on a device with sm_count SMs and tiles_x tiles per row; 0 where
 // prefetching is off.
 int collide_stream_prefetch_rows(int storage, int sm_count, int tiles_x);
-cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st);
+// priority: the launch's scheduling priority (0: the stream's own; lower
+// numbers are served first)
+cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st, int priority = 0);
 cudaError_t launch_gather(int storage, const void *pop, const uint16_t *nbits, const void *inlet,
                           long long plane, int nx, int ny, int pitch, int periodic,
                           int precollision, double rho0, int plane_i, double *out,

@@ -277,16 +277,27 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
     }
 }
 
-cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st)
+cudaError_t launch_link_force(int storage, const LinkArgs &a, cudaStream_t st, int priority)
 {
-    const int grid = a.n_ctas;
+    // The priority travels with the launch, so that a captured graph node
+    // keeps it: the link kernel runs beside a collide-stream kernel that
+    // fills the GPU, and the collide-stream kernel two steps on waits for it.
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = priority;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.n_ctas);
+    cfg.blockDim = dim3(LINK_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = priority != 0 ? 1 : 0;
     switch (storage) {
-    case LBM_F64: k_link_force<LBM_F64><<<grid, LINK_THREADS, 0, st>>>(a); break;
-    case LBM_F32: k_link_force<LBM_F32><<<grid, LINK_THREADS, 0, st>>>(a); break;
-    case LBM_F32_DEV: k_link_force<LBM_F32_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
-    default: k_link_force<LBM_F16_DEV><<<grid, LINK_THREADS, 0, st>>>(a); break;
+    case LBM_F64: return cudaLaunchKernelEx(&cfg, k_link_force<LBM_F64>, a);
+    case LBM_F32: return cudaLaunchKernelEx(&cfg, k_link_force<LBM_F32>, a);
+    case LBM_F32_DEV: return cudaLaunchKernelEx(&cfg, k_link_force<LBM_F32_DEV>, a);
+    default: return cudaLaunchKernelEx(&cfg, k_link_force<LBM_F16_DEV>, a);
     }
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -338,7 +338,9 @@ __global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int 
                              typename Traits<S>::store_t *__restrict__ inlet)
 {
     using ST = typename Traits<S>::store_t;
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per row; lane l tries the choices l, l + 32, ... of the 2^9
+    const int y = blockIdx.x * (blockDim.x / 32) + (int)(threadIdx.x / 32);
+    const int lane = threadIdx.x & 31;
     if (y >= ny) return;
     const double u = u_row[y];
     double v[9];
@@ -348,8 +350,9 @@ __global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int 
         if (Traits<S>::dev) v[i] -= wgt<double>(i) * rho0;
     }
     if constexpr (S == LBM_F64) {
+        if (lane == 0)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) inlet[i * ny + y] = v[i];
+            for (int i = 0; i < 9; ++i) inlet[i * ny + y] = v[i];
     } else {
         ST lo[9], hi[9];
         double dl[9], dh[9];
@@ -360,7 +363,7 @@ __global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int 
         }
         unsigned best = 0;
         double best_e = INFINITY, best_a = INFINITY;
-        for (unsigned c = 0; c < 512u; ++c) {
+        for (unsigned c = lane; c < 512u; c += 32) {
             double dr = 0.0, jx = 0.0, jy = 0.0, ab = 0.0;
             for (int i = 0; i < 9; ++i) {
                 const double d = (c >> i) & 1u ? dh[i] : dl[i];
@@ -376,7 +379,20 @@ __global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int 
                 best = c;
             }
         }
-        for (int i = 0; i < 9; ++i) inlet[i * ny + y] = (best >> i) & 1u ? hi[i] : lo[i];
+        // the warp's best: least error, then least total rounding, then the
+        // lowest choice index (the same winner as a serial search)
+        for (int d = 16; d > 0; d >>= 1) {
+            const double oe = __shfl_xor_sync(0xffffffffu, best_e, d);
+            const double oa = __shfl_xor_sync(0xffffffffu, best_a, d);
+            const unsigned oc = __shfl_xor_sync(0xffffffffu, best, d);
+            if (oe < best_e || (oe == best_e && (oa < best_a || (oa == best_a && oc < best)))) {
+                best_e = oe;
+                best_a = oa;
+                best = oc;
+            }
+        }
+        if (lane == 0)
+            for (int i = 0; i < 9; ++i) inlet[i * ny + y] = (best >> i) & 1u ? hi[i] : lo[i];
     }
 }
 
@@ -402,7 +418,7 @@ cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *
                         cudaStream_t st)
 {
     dim3 grid((nx + 255) / 256, ny);
-    const int rb = (ny + 127) / 128;
+    const int rb = (ny + 3) / 4;  // four rows (warps) a block
     switch (storage) {
     case LBM_F64:
         k_inlet_rows<LBM_F64><<<rb, 128, 0, st>>>(u_row, rho0, ny, (double *)inlet);
