@@ -244,15 +244,31 @@ lbm_status lbm_cylinder_mask(int nx, int ny, double xc, double yc, double diamet
  *   dJ_dtau     dJ/dtau;
  *   dJ_du[ny]   dJ/du_in(y) through the equilibrium inlet of every row;
  *   dJ_df0      [9][ny][nx] dJ/df(x, T0), pre-collision state at T0 (0 on solid
- *               nodes and in the inlet column, which do not enter J).
+ *               nodes and in the inlet column, which do not enter J); host
+ *               memory, or device memory of the handle's device (unified
+ *               addressing tells them apart), where it is written in place
+ *               without a copy to the host.
  * Every step of the forward map (BGK collision, pull streaming with halfway
  * bounce-back, inlet, outlet) is differentiated exactly and transposed, in the
- * storage's compute precision; states are recomputed from checkpoints every
- * checkpoint_every steps (<= 0: ceil(sqrt(steps))).  Any output may be NULL.
+ * storage's compute precision.  checkpoint_every > 0: states are recomputed
+ * from checkpoints taken every checkpoint_every steps.  checkpoint_every <= 0:
+ * the forward pass keeps the states of the last L steps in device memory
+ * (no recompute for them), L as large as 60 % of the free device memory
+ * (or lbm_set_adjoint_budget) allows, and the first steps - L are checkpointed every
+ * ceil(sqrt(steps - L)) steps; the results are the same bits either way.
+ * Any output may be NULL.
+ * Synchronous: every output is complete when the call returns.
  * EINVAL for a periodic domain, a body force, record_series = 0, or
  * window outside [1, steps]. */
 lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, int checkpoint_every,
                        double *J, double *dJ_dtau, double *dJ_du, double *dJ_df0);
+
+/* Device memory, in bytes, that lbm_adjoint with checkpoint_every <= 0 may
+ * fill with kept states and checkpoints (0, the default: 60 % of the free
+ * device memory at the call).  A caller whose allocator holds cached memory
+ * that cudaMemGetInfo does not count as free states what it can provide.
+ * Host-side only; EINVAL for a negative or non-finite value. */
+lbm_status lbm_set_adjoint_budget(lbm_ctx *h, double bytes);
 
 /* Number of completed steps T. */
 long lbm_steps_done(const lbm_ctx *h);

@@ -19,9 +19,11 @@ class ForceObjective(torch.autograd.Function):
         u = u_in.detach().to("cpu", torch.float64).numpy()
         lat = binding.Lattice(m, float(tau), u, storage=storage)
         lat.set_populations(f0.detach().to("cpu", torch.float64).numpy())
-        J, dtau, du, df0 = lat.adjoint(int(steps), int(window), float(wx), float(wy))
+        # a CUDA f0 gets its gradient straight from device memory
+        J, dtau, du, df0 = lat.adjoint(int(steps), int(window), float(wx), float(wy), df0_device=f0.is_cuda)
         lat.close()
-        ctx.save_for_backward(torch.from_numpy(df0).to(f0.device, f0.dtype),
+        df0 = df0 if f0.is_cuda else torch.from_numpy(df0)
+        ctx.save_for_backward(df0.to(f0.device, f0.dtype),
                               torch.tensor(dtau, dtype=tau.dtype, device=tau.device),
                               torch.from_numpy(du).to(u_in.device, u_in.dtype))
         return torch.tensor(J, dtype=torch.float64)

@@ -92,10 +92,12 @@ def lib():
     L.lbm_set_kernel.argtypes = [vp, C.c_int]
     L.lbm_set_wait_limit.argtypes = [vp, C.c_long]
     L.lbm_coefficients.argtypes = [vp, C.c_int, C.c_long, C.c_long, C.c_double, C.c_double, dp, dp, dp]
+    L.lbm_set_adjoint_budget.argtypes = [vp, C.c_double]
     for name in ("lbm_create", "lbm_step", "lbm_force", "lbm_force_series", "lbm_populations",
                  "lbm_set_populations", "lbm_links", "lbm_control_volume", "lbm_naca_mask",
                  "lbm_set_kernel_timing", "lbm_kernel_times", "lbm_adjoint", "lbm_prepare",
-                 "lbm_coefficients", "lbm_set_kernel", "lbm_set_wait_limit", "lbm_step_async", "lbm_sync"):
+                 "lbm_coefficients", "lbm_set_kernel", "lbm_set_wait_limit", "lbm_step_async", "lbm_sync",
+                 "lbm_set_adjoint_budget"):
         getattr(L, name).restype = C.c_int
     # batches
     L.lbm_batch_create.argtypes = [C.POINTER(lbm_domain), C.c_int, C.POINTER(lbm_bc), C.POINTER(vp)]
@@ -183,6 +185,21 @@ def body_mask(w):
     return naca_mask(w.nx, w.ny, w.chord, w.thickness, w.alpha_deg, w.xc, w.yc)
 
 
+_STREAMS = {}
+
+
+def default_stream(device=0):
+    """The stream handles use when none is given: one per device, so that the
+    memory one handle returns to torch's caching allocator (which reuses a
+    block on the stream it was freed on) serves the next handle.  The library
+    frees memory only after its stream is idle."""
+    import torch
+    s = _STREAMS.get(device)
+    if s is None:
+        s = _STREAMS[device] = torch.cuda.Stream(device)
+    return s
+
+
 class _TorchAllocator:
     """Device memory for the library from torch's caching allocator."""
 
@@ -219,7 +236,7 @@ class Lattice:
         self.mask = np.ascontiguousarray(mask, np.uint8)
         self.ny, self.nx = self.mask.shape
         self.device = device
-        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        self.stream = stream if stream is not None else default_stream(device)
         u = np.ascontiguousarray(np.atleast_1d(np.asarray(u_in, np.float64)))
         bc = lbm_bc()
         L.lbm_bc_default(C.byref(bc))
@@ -344,15 +361,31 @@ class Lattice:
         _check(lib().lbm_control_volume(self._h, cv), self._h)
         return list(cv)
 
-    def adjoint(self, steps, window, wx=1.0, wy=0.0, checkpoint_every=0, want_df0=True):
+    def adjoint(self, steps, window, wx=1.0, wy=0.0, checkpoint_every=0, want_df0=True, df0_device=False):
         """Run `steps` steps and return (J, dJ/dtau, dJ/du_in[ny], dJ/df0[9][ny][nx] or
-        None) for J = the window-averaged wx Fx + wy Fy of algorithm B."""
+        None) for J = the window-averaged wx Fx + wy Fy of algorithm B.
+        df0_device: dJ/df0 as a float64 CUDA tensor on the handle's device,
+        written there by the library (no copy to the host); else a numpy array."""
         J, dtau = C.c_double(), C.c_double()
         du = np.zeros(self.ny)
-        df0 = np.zeros((9, self.ny, self.nx)) if want_df0 else None
+        df0, ptr = None, None
+        if checkpoint_every <= 0 and self._alloc is not None:
+            # what torch can provide: the free memory and its own unused cache
+            import torch
+            free, _ = torch.cuda.mem_get_info(self.device)
+            cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+            _check(lib().lbm_set_adjoint_budget(self._h, 0.6 * float(free + cached)), self._h)
+        if want_df0 and df0_device:
+            import torch
+            df0 = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.device)
+            # the handle's stream writes the block torch allocated on its current stream
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+            ptr = C.cast(C.c_void_p(df0.data_ptr()), C.POINTER(C.c_double))
+        elif want_df0:
+            df0 = np.empty((9, self.ny, self.nx))
+            ptr = _dp(df0)
         _check(lib().lbm_adjoint(self._h, int(steps), int(window), float(wx), float(wy),
-                                 int(checkpoint_every), C.byref(J), C.byref(dtau), _dp(du),
-                                 _dp(df0) if df0 is not None else None), self._h)
+                                 int(checkpoint_every), C.byref(J), C.byref(dtau), _dp(du), ptr), self._h)
         return J.value, dtau.value, du, df0
 
     def pressure_coefficient(self, p_inf=None, q=None):
@@ -410,7 +443,7 @@ class Batch:
         import torch
         L = lib()
         self.device = device
-        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        self.stream = stream if stream is not None else default_stream(device)
         self._keep = []
         arr = (lbm_domain * len(domains))()
         self.shapes = []

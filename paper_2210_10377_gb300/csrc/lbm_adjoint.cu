@@ -27,6 +27,7 @@ struct AdjArgs {
     const void *lam_next;  // [9][ny][pitch] compute type: lam(t+1)
     void *lam;             // [9][ny][pitch] compute type: lam(t)
     const uint16_t *nbits;
+    const uint8_t *tile_flag;  // per tile of the grid: 0 = every node's bits are 0 (or NULL)
     const double *u_row;
     double *du_acc;        // [ny] running dJ/du_in
     double *dw_acc;        // [gridDim.x * gridDim.y] running per-block dJ/domega
@@ -215,6 +216,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, GBLBM_ADJ_MINB) k_adjoint_step(Ad
     adj_prefetch<S>(a);
     const int x = blockIdx.x * ADJ_TX + threadIdx.x;
     const int y0 = blockIdx.y * ADJ_TR + threadIdx.y * ADJ_RPT;
+    // a tile whose nodes all have zero bits (no solid in or next to it) skips
+    // the per-node bit loads, so its population loads start at once
+    const bool plain_tile =
+        a.tile_flag && !a.precollision && a.tile_flag[(long long)blockIdx.y * gridDim.x + blockIdx.x] == 0;
     Acc dw;
     acc_zero(dw);
     if (x < a.nx) {
@@ -224,9 +229,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, GBLBM_ADJ_MINB) k_adjoint_step(Ad
 #pragma unroll
         for (int r = 0; r < ADJ_RPT; ++r) {
             const int y = y0 + r;
+            nb[r] = (plain_tile || y >= a.ny) ? (uint16_t)0 : a.nbits[(long long)y * a.pitch + x];
+        }
+#pragma unroll
+        for (int r = 0; r < ADJ_RPT; ++r) {
+            const int y = y0 + r;
             live[r] = false;
             if (y >= a.ny) continue;
-            nb[r] = a.nbits[(long long)y * a.pitch + x];
             live[r] = adj_node_inputs<S>(a, x, y, nb[r], lt[r], g[r]);
         }
 #pragma unroll
@@ -284,7 +293,8 @@ int adjoint_blocks(int nx, int ny)
 }
 
 cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, const void *lam_next, void *lam,
-                                const uint16_t *nbits, const double *u_row, double *du_acc,
+                                const uint16_t *nbits, const uint8_t *tile_flag, int flag_rows, int flag_tiles_x,
+                                const double *u_row, double *du_acc,
                                 double *dw_acc, long long plane, int nx, int ny, int pitch,
                                 int in_window, double omega, double rho0, double obj_x,
                                 double obj_y, cudaStream_t st)
@@ -313,6 +323,9 @@ cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, 
     }
     dim3 grid((nx + ADJ_TX - 1) / ADJ_TX, (ny + ADJ_TR - 1) / ADJ_TR);
     dim3 block(ADJ_TX, ADJ_TR / ADJ_RPT);
+    // the collide-stream tile flags serve when their tiles are these tiles
+    a.tile_flag = (tile_flag && TILE_X == ADJ_TX && flag_rows == ADJ_TR && flag_tiles_x == (int)grid.x) ? tile_flag
+                                                                                                        : nullptr;
     // prefetch half the CTAs the GPU holds at once ahead, in tile rows
     int pf_rows = 0;
     if (storage != LBM_F64) {
@@ -340,6 +353,39 @@ cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, 
 cudaError_t launch_sum_fixed(const double *v, long long n, double *out, cudaStream_t st)
 {
     k_sum_fixed<<<1, 256, 0, st>>>(v, n, out);
+    return cudaGetLastError();
+}
+
+// dJ/df(x, T0) = lambda(T0) in FP64, [9][ny][nx] without the row pitch: zero on
+// solid nodes and in the inlet column, which do not enter J.  One thread per
+// (direction, node); the conversion from FP32 is exact.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adjoint_df0(const C *__restrict__ lam, const uint8_t *__restrict__ mask,
+                                                     long long plane, int nx, int ny, int pitch,
+                                                     double *__restrict__ out)
+{
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * 256LL + threadIdx.x; k < 9 * n; k += (long long)gridDim.x * 256) {
+        const int i = (int)(k / n);
+        const long long node = k - i * n;
+        const int y = (int)(node / nx), x = (int)(node - (long long)y * nx);
+        const double v = (double)lam[i * plane + (long long)y * pitch + x];
+        out[k] = (mask[node] || x == 0) ? 0.0 : v;
+    }
+}
+
+cudaError_t launch_adjoint_df0(int storage, const void *lam, const uint8_t *mask, long long plane, int nx, int ny,
+                               int pitch, int sm_count, double *out, cudaStream_t st)
+{
+    const long long total = 9LL * nx * ny;
+    long long blocks = (total + 255) / 256;
+    const long long cap = 8LL * (sm_count > 0 ? sm_count : 1);
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (storage == LBM_F64)
+        k_adjoint_df0<double><<<(int)blocks, 256, 0, st>>>((const double *)lam, mask, plane, nx, ny, pitch, out);
+    else
+        k_adjoint_df0<float><<<(int)blocks, 256, 0, st>>>((const float *)lam, mask, plane, nx, ny, pitch, out);
     return cudaGetLastError();
 }
 

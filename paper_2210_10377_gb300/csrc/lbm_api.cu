@@ -31,6 +31,12 @@ constexpr int NBUF = 3;
 #endif
 constexpr int GRAPH_STEPS = GBLBM_GRAPH_STEPS;  // steps per captured graph (a multiple of NBUF)
 static_assert(GRAPH_STEPS % NBUF == 0 && GRAPH_STEPS >= NBUF, "GRAPH_STEPS: a multiple of NBUF");
+// Share of the free device memory the adjoint may fill with kept forward
+// states when the caller leaves the checkpoint interval to it (a tuning knob).
+#ifndef GBLBM_ADJ_KEEP_SHARE
+#define GBLBM_ADJ_KEEP_SHARE 0.6
+#endif
+constexpr double ADJ_KEEP_SHARE = GBLBM_ADJ_KEEP_SHARE;
 constexpr int TIMING_BATCH = 64;
 
 }  // namespace
@@ -66,6 +72,7 @@ struct lbm_ctx {
     // collide-stream kernel, or when the queue ends.
     int lead_src = -1, lead_pre = 0;
     int link_prio = 0;           // launch priority of the link kernels (the device's highest)
+    double adj_budget = 0;       // bytes the adjoint may fill with kept states (0: from free memory)
     uint8_t *mask_d = nullptr;
     uint16_t *nbits = nullptr;
     uint8_t *tile_flag = nullptr;
@@ -763,6 +770,48 @@ lbm_status queue_steps(lbm_ctx *h, int n)
     return LBM_OK;
 }
 
+// Queues n eager steps whose states are kept for a backward sweep: step j
+// (0-based) reads slot j and writes slot j + 1 of `slots` (stride bytes
+// apart; slot 0 holds a copy of the current state), except the last step,
+// which writes the handle's own next buffer.  Each step points the logical
+// buffer it writes at its slot, so the kernels, the held link kernels and the
+// force series are exactly those of queue_steps; only the population
+// addresses differ.  The direct collide-stream kernel serves these steps (the
+// staged kernel's tensor maps describe the handle's own buffers).
+lbm_status queue_steps_keep(lbm_ctx *h, int n, char *slots, size_t stride)
+{
+    lbm_status st = ensure_series(h, h->t + n);
+    if (st != LBM_OK) return st;
+    if (!h->status_armed) {
+        CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
+        CK(h, cudaMemsetAsync(h->status + 1, 0x7f, sizeof(int), h->stream), "status reset");
+        h->status_armed = true;
+    }
+    void *orig[NBUF];
+    for (int b = 0; b < NBUF; ++b) orig[b] = h->pop[b];
+    const int bulk = h->use_bulk;
+    h->use_bulk = 0;
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < n && e == cudaSuccess; ++j) {
+        const int db = next_buf(h->cur);
+        // the held link kernel of step j-1 reads buffers prev(cur) and cur,
+        // whose addresses stay as they were
+        h->pop[db] = j + 1 < n ? (void *)(slots + (size_t)(j + 1) * stride) : orig[db];
+        e = launch_one_step(h, h->cur, h->precollision, nullptr);
+        h->cur = db;
+        h->precollision = 0;
+        h->t += 1;
+    }
+    if (e == cudaSuccess) e = flush_link(h);
+    if (e == cudaSuccess) e = join_side(h);
+    // launches took their arguments by value: the handle's buffers are its own again
+    for (int b = 0; b < NBUF; ++b) h->pop[b] = orig[b];
+    h->use_bulk = bulk;
+    h->pending = true;
+    if (e != cudaSuccess) return cuda_err(h, e, "adjoint forward steps");
+    return LBM_OK;
+}
+
 // Waits for the queued steps and turns their status words into a result.
 lbm_status settle(lbm_ctx *h)
 {
@@ -1105,18 +1154,43 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
         return set_err(h, LBM_EINVAL, "the adjoint does not cover a body force");
     if (!h->record_series) return set_err(h, LBM_EINVAL, "the adjoint needs record_series = 1");
     if (!std::isfinite(wx) || !std::isfinite(wy)) return set_err(h, LBM_EINVAL, "weights not finite");
-    int K = checkpoint_every;
-    if (K <= 0) {
-        K = 1;
-        while ((long long)K * K < steps) ++K;
-    }
-    if (K > steps) K = steps;
-    const int nck = (steps + K - 1) / K;
     const size_t buf_bytes = 9 * (size_t)h->plane * h->elem;
     const size_t comp = h->storage == LBM_F64 ? 8 : 4;
     const size_t comp_bytes = 9 * (size_t)h->plane * comp;
     const int nblk = adjoint_blocks(h->nx, h->ny);
     cudaStream_t st = h->stream;
+    auto isqrt_up = [](long long n) {
+        long long k = 1;
+        while (k * k < n) ++k;
+        return (int)k;
+    };
+    // Plan.  The last L steps keep the states the forward pass writes (no
+    // recompute); the first F = steps - L are checkpointed every K steps and
+    // recomputed segment by segment.  With checkpoint_every <= 0, L is as
+    // large as ADJ_KEEP_SHARE of the free device memory allows, counting the
+    // checkpoints and segment buffers the first F steps then need.
+    int L = 0;
+    if (checkpoint_every <= 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        const double reserve = 2.0 * comp_bytes + 72.0 * h->nx * h->ny + (double)(1u << 30);
+        const double avail = (h->adj_budget > 0 ? h->adj_budget : ADJ_KEEP_SHARE * (double)fr) - reserve;
+        const long long slots = avail > 0 ? (long long)(avail / (double)buf_bytes) : 0;
+        auto need = [&](long long keep) {
+            const long long f = steps - keep;
+            if (f <= 0) return keep;
+            const long long k = isqrt_up(f);
+            return keep + (f + k - 1) / k + (k - 1);
+        };
+        for (long long keep = slots < steps ? slots : steps; keep > 0; --keep)
+            if (need(keep) <= slots) {
+                L = (int)keep;
+                break;
+            }
+    }
 
     std::vector<void *> owned;
     auto grab = [&](size_t bytes) {
@@ -1129,17 +1203,25 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
         for (void *p : owned) dev_free(h, p);
         owned.clear();
     };
+    // the kept states of the last L steps (slot j: the state step F + j reads)
+    char *keep = L > 0 ? (char *)grab(buf_bytes * (size_t)L) : nullptr;
+    if (!keep) L = 0;  // no room after all: checkpoints only
+    const int F = steps - L;
+    int K = checkpoint_every > 0 ? checkpoint_every : isqrt_up(F);
+    if (K > F) K = F > 0 ? F : 1;
+    const int nck = F > 0 ? (F + K - 1) / K : 0;
     // checkpoints; the recomputed post-collision states of one segment (the
     // first step of a segment reads its checkpoint, step s > 0 the state
     // written by step s-1, so K-1 buffers); the adjoint pair lam(t+1), lam(t)
-    char *ck = (char *)grab(buf_bytes * nck);
-    char *seg = K > 1 ? (char *)grab(buf_bytes * (K - 1)) : nullptr;
+    char *ck = nck > 0 ? (char *)grab(buf_bytes * nck) : nullptr;
+    char *seg = nck > 0 && K > 1 ? (char *)grab(buf_bytes * (K - 1)) : nullptr;
     char *lam_a = (char *)grab(comp_bytes), *lam_b = (char *)grab(comp_bytes);
     double *part = (double *)grab(sizeof(double) * CV_PARTIAL * h->n_cv_tiles);
     double *du_acc = (double *)grab(sizeof(double) * h->ny);
     double *dw_acc = (double *)grab(sizeof(double) * nblk);
     double *dw_out = (double *)grab(sizeof(double));
-    if (!ck || (K > 1 && !seg) || !lam_a || !lam_b || !part || !du_acc || !dw_acc || !dw_out) {
+    if ((nck > 0 && !ck) || (nck > 0 && K > 1 && !seg) || !lam_a || !lam_b || !part || !du_acc || !dw_acc ||
+        !dw_out) {
         release();
         return set_err(h, LBM_ENOMEM, "adjoint: allocation of checkpoints / work arrays failed");
     }
@@ -1155,8 +1237,24 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
             return cuda_err(h, e, "adjoint: checkpoint copy");
         }
         ckpre[k] = h->precollision;
-        const int n = (k + 1) * K <= steps ? K : steps - k * K;
+        const int n = (k + 1) * K <= F ? K : F - k * K;
         rs = lbm_step(h, n);
+        if (rs != LBM_OK) {
+            release();
+            return rs;
+        }
+    }
+    // the kept steps write their states into the slots as they go
+    int keep_pre = 0;
+    if (L > 0) {
+        cudaError_t e = cudaMemcpyAsync(keep, h->pop[h->cur], buf_bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            release();
+            return cuda_err(h, e, "adjoint: state copy");
+        }
+        keep_pre = h->precollision;
+        rs = queue_steps_keep(h, L, keep, buf_bytes);
+        if (rs == LBM_OK) rs = settle(h);
         if (rs != LBM_OK) {
             release();
             return rs;
@@ -1182,9 +1280,21 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
     if (e == cudaSuccess) e = cudaMemsetAsync(dw_acc, 0, sizeof(double) * nblk, st);
     char *lam_next = lam_b, *lam_cur = lam_a;  // lam(T) = 0
     const double obj_x = 2.0 * wx / window, obj_y = 2.0 * wy / window;
+    // the kept steps, last to first: their states need no recompute
+    for (int j = L - 1; j >= 0 && e == cudaSuccess; --j) {
+        const int t = F + j;
+        e = launch_adjoint_step(h->storage, keep + buf_bytes * (size_t)j, j == 0 ? keep_pre : 0, lam_next, lam_cur,
+                                h->nbits, h->tile_flag, tile_rows(h->storage), h->tiles_x, h->u_row, du_acc, dw_acc,
+                                h->plane, h->nx, h->ny, h->pitch, t >= steps - window, h->omega, h->rho0, obj_x,
+                                obj_y, st);
+        char *tmp = lam_next;
+        lam_next = lam_cur;
+        lam_cur = tmp;
+        h->launches += 1;
+    }
     for (int k = nck - 1; k >= 0 && e == cudaSuccess; --k) {
         const int t0 = k * K;
-        const int n = (k + 1) * K <= steps ? K : steps - t0;
+        const int n = (k + 1) * K <= F ? K : F - t0;
         // the state step t0 + s reads
         auto state = [&](int s) { return s == 0 ? ck + buf_bytes * k : seg + buf_bytes * (s - 1); };
         for (int s = 0; s + 1 < n && e == cudaSuccess; ++s) {
@@ -1199,7 +1309,8 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
         for (int s = n - 1; s >= 0 && e == cudaSuccess; --s) {
             const int t = t0 + s;
             e = launch_adjoint_step(h->storage, state(s), s == 0 ? ckpre[k] : 0, lam_next, lam_cur, h->nbits,
-                                    h->u_row, du_acc, dw_acc, h->plane, h->nx, h->ny, h->pitch,
+                                    h->tile_flag, tile_rows(h->storage), h->tiles_x, h->u_row, du_acc, dw_acc,
+                                    h->plane, h->nx, h->ny, h->pitch,
                                     t >= steps - window, h->omega, h->rho0, obj_x, obj_y, st);
             char *tmp = lam_next;
             lam_next = lam_cur;
@@ -1213,10 +1324,26 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&dw, dw_out, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(du.data(), du_acc, sizeof(double) * h->ny, cudaMemcpyDeviceToHost, st);
-    std::vector<char> lam_host;
+    // dJ/df0 = lambda(T0) in FP64, assembled on the device: straight into
+    // dJ_df0 when it is device memory, else into a scratch array copied once
     if (e == cudaSuccess && dJ_df0) {
-        lam_host.resize(comp_bytes);
-        e = cudaMemcpyAsync(lam_host.data(), lam_next, comp_bytes, cudaMemcpyDeviceToHost, st);
+        const size_t N = (size_t)h->nx * h->ny;
+        cudaPointerAttributes pa;
+        bool on_device = false;
+        if (cudaPointerGetAttributes(&pa, dJ_df0) == cudaSuccess)
+            on_device = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+        else
+            cudaGetLastError();
+        double *out = on_device ? dJ_df0 : (double *)grab(sizeof(double) * 9 * N);
+        if (!out) {
+            release();
+            return set_err(h, LBM_ENOMEM, "adjoint: allocation of the dJ/df0 array failed");
+        }
+        e = launch_adjoint_df0(h->storage, lam_next, h->mask_d, h->plane, h->nx, h->ny, h->pitch, h->sm_count, out,
+                               st);
+        h->launches += 1;
+        if (e == cudaSuccess && !on_device)
+            e = cudaMemcpyAsync(dJ_df0, out, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     release();
@@ -1224,22 +1351,14 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
     if (dJ_dtau) *dJ_dtau = -dw / (h->tau * h->tau);
     if (dJ_du)
         for (int y = 0; y < h->ny; ++y) dJ_du[y] = du[y];
-    if (dJ_df0) {
-        // lam(T0) = dJ/df(T0) on fluid nodes; the inlet column and solid nodes do not enter J
-        const size_t N = (size_t)h->nx * h->ny;
-        std::vector<uint8_t> mask(N);
-        cudaError_t me = cudaMemcpy(mask.data(), h->mask_d, N, cudaMemcpyDeviceToHost);
-        if (me != cudaSuccess) return cuda_err(h, me, "adjoint: mask read-back");
-        for (int i = 0; i < 9; ++i)
-            for (int y = 0; y < h->ny; ++y)
-                for (int x = 0; x < h->nx; ++x) {
-                    const size_t src = (size_t)i * h->plane + (size_t)y * h->pitch + x;
-                    double v = comp == 8 ? ((const double *)lam_host.data())[src]
-                                         : (double)((const float *)lam_host.data())[src];
-                    if (mask[(size_t)y * h->nx + x] || x == 0) v = 0.0;
-                    dJ_df0[(size_t)i * N + (size_t)y * h->nx + x] = v;
-                }
-    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_adjoint_budget(lbm_ctx *h, double bytes)
+{
+    if (!h) return set_err(nullptr, LBM_EINVAL, "NULL handle");
+    if (!(bytes >= 0) || !std::isfinite(bytes)) return set_err(h, LBM_EINVAL, "budget must be finite and >= 0");
+    h->adj_budget = bytes;
     return LBM_OK;
 }
 

@@ -14,19 +14,18 @@
 namespace gblbm {
 
 // Minimum resident CTAs per SM asked of the compiler for the one-CTA-per-tile
-// form (0: no bound), per storage: 2 x 512 threads (64 registers) for FP32,
-// 4 x 256 for FP16 deviations (1024-node tiles; both measured best with the
-// packed collision).  The persistent form carries no bound: its tile loop
+// form (0: no bound), per storage: 8 x 128 threads (64 registers) for FP32
+// and for FP16 deviations (both measured best).  The persistent form carries no bound: its tile loop
 // keeps the domain arguments live across tiles and needs about 128 registers
 // a thread.
 #ifndef GBLBM_BATCH_MINB_F64
 #define GBLBM_BATCH_MINB_F64 0
 #endif
 #ifndef GBLBM_BATCH_MINB_F32
-#define GBLBM_BATCH_MINB_F32 2
+#define GBLBM_BATCH_MINB_F32 8
 #endif
 #ifndef GBLBM_BATCH_MINB_F16
-#define GBLBM_BATCH_MINB_F16 4
+#define GBLBM_BATCH_MINB_F16 8
 #endif
 template <int S> struct BatchMinBlocks {
     static constexpr int value = S == LBM_F64       ? GBLBM_BATCH_MINB_F64

@@ -26,13 +26,15 @@ namespace gblbm {
 #endif
 constexpr int BATCH_SHAPES = 3;
 __host__ __device__ constexpr int batch_tx(int shape) { return shape == 0 ? 128 : (shape == 1 ? 64 : 32); }
-// Rows of the 128-wide shape: 8 for FP32 and FP16 deviations (1024 nodes, so
-// that the per-tile domain look-up is spread over as many nodes), 4 for FP64
+// Rows of the 128-wide shape: 2 for FP32 (256-node tiles of 128 threads), 4
+// for FP16 deviations (512-node tiles of 128 threads), 4 for FP64.  Small CTAs,
+// eight to an SM, overlap more tiles' dependent starts (tile entry, domain
+// arguments, populations) than the 1024-node tiles did.
 #ifndef GBLBM_BATCH_ROWS_F16
-#define GBLBM_BATCH_ROWS_F16 8
+#define GBLBM_BATCH_ROWS_F16 4
 #endif
 #ifndef GBLBM_BATCH_ROWS_F32
-#define GBLBM_BATCH_ROWS_F32 8
+#define GBLBM_BATCH_ROWS_F32 2
 #endif
 __host__ __device__ constexpr int batch_tr(int storage, int shape)
 {

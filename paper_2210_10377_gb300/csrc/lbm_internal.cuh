@@ -247,11 +247,18 @@ cudaError_t launch_scatter_pop(int storage, void *pop, const uint16_t *nbits, lo
 // discrete adjoint (lbm_adjoint.cu): one backward step; src holds ft(t-1) in
 // the storage type (f(t) itself when precollision), pulled inside the kernel
 int adjoint_blocks(int nx, int ny);
+// tile_flag: the collide-stream tile flags (tiles of TILE_X x flag_rows nodes,
+// flag_tiles_x a row), used when they match the backward step's tiles
 cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, const void *lam_next, void *lam,
-                                const uint16_t *nbits, const double *u_row, double *du_acc,
+                                const uint16_t *nbits, const uint8_t *tile_flag, int flag_rows, int flag_tiles_x,
+                                const double *u_row, double *du_acc,
                                 double *dw_acc, long long plane, int nx, int ny, int pitch,
                                 int in_window, double omega, double rho0, double obj_x,
                                 double obj_y, cudaStream_t st);
 cudaError_t launch_sum_fixed(const double *v, long long n, double *out, cudaStream_t st);
+// lambda (compute type, [9][ny][pitch]) -> dJ/df0 in FP64 [9][ny][nx] in device
+// memory, zero on solid nodes (mask) and in the inlet column
+cudaError_t launch_adjoint_df0(int storage, const void *lam, const uint8_t *mask, long long plane, int nx, int ny,
+                               int pitch, int sm_count, double *out, cudaStream_t st);
 
 }  // namespace gblbm

@@ -108,6 +108,7 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.lbm_step(None, 1) == 1
     assert L.lbm_force(None, 0, C.byref(fx), C.byref(fy)) == 1
     assert L.lbm_steps_done(None) == -1
+    assert L.lbm_set_adjoint_budget(None, 1.0) == 1
     L.lbm_destroy(None)
 
 

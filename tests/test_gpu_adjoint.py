@@ -52,6 +52,43 @@ def test_f64_adjoint_matches_oracle_adjoint(gb, K):
     assert np.abs(dfg - dfo).max() <= 1e-9 * np.abs(dfo).max()
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32dev", "f16dev"])
+def test_kept_states_give_the_bits_of_recomputed_states(gb, storage):
+    # checkpoint_every = 0 keeps every forward state in device memory (a small
+    # grid fits), K = 7 recomputes them from checkpoints: same kernels, same
+    # states, so the same bits; the handle ends in the same state
+    m, u, f0 = small_case(13)
+    outs, pops = [], []
+    for K in (0, 7):
+        lat = gb.Lattice(m, 0.7, u, storage=storage)
+        lat.set_populations(f0)
+        outs.append(lat.adjoint(90, 40, 0.3, -0.9, checkpoint_every=K))
+        pops.append(lat.populations())
+        lat.close()
+    (J0, t0, u0, d0), (J1, t1, u1, d1) = outs
+    assert J0 == J1 and t0 == t1
+    assert np.array_equal(u0, u1) and np.array_equal(d0, d1)
+    assert np.array_equal(pops[0], pops[1])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32dev"])
+def test_df0_in_device_memory_equals_the_host_copy(gb, storage):
+    # dJ/df0 written in place into a CUDA tensor equals the host read-back bit
+    # for bit, and is zero on solid nodes and in the inlet column
+    import torch
+    m, u, f0 = small_case(11)
+    Jh, th, uh, dh = gpu_adjoint(gb, m, 0.7, u, f0, 90, 40, 0.8, 0.6, storage)
+    lat = gb.Lattice(m, 0.7, u, storage=storage)
+    lat.set_populations(f0)
+    Jd, td, ud, dd = lat.adjoint(90, 40, 0.8, 0.6, df0_device=True)
+    lat.close()
+    assert dd.is_cuda and dd.dtype == torch.float64 and tuple(dd.shape) == dh.shape
+    assert np.array_equal(dd.cpu().numpy(), dh)
+    assert Jd == Jh and td == th and np.array_equal(ud, uh)
+    assert np.all(dh[:, m != 0] == 0.0) and np.all(dh[:, :, 0] == 0.0)
+    assert np.abs(dh).max() > 0.0
+
+
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-3), ("f32dev", 1e-3)])
 def test_reduced_precision_adjoint_matches_oracle(gb, storage, tol):
     w = inputs.scaled(inputs.DIFF, 4)  # 128 x 64, chord 16 at 2 deg, same tau
@@ -122,17 +159,19 @@ def test_differentiation_workload_against_central_differences(gb, wx, wy):
     assert abs(J - J64()) <= 1e-3 * abs(J)
 
 
-def test_autograd_function(gb):
+@pytest.mark.parametrize("device", ["cpu", "cuda"])
+def test_autograd_function(gb, device):
     import torch
     from paper_2210_10377_gb300.autograd import force_objective
     m, u, f0 = small_case(9)
-    f = torch.tensor(f0, dtype=torch.float64, requires_grad=True)
+    f = torch.tensor(f0, dtype=torch.float64, device=device, requires_grad=True)
     tau = torch.tensor(0.7, dtype=torch.float64, requires_grad=True)
     uu = torch.tensor(u, dtype=torch.float64, requires_grad=True)
     J = force_objective(f, tau, uu, m, 60, 30, 1.0, 0.0, "f64")
     (3.0 * J).backward()
     Jo, dto, duo, dfo = oracle.adjoint(m, 0.7, u, f0, 60, 30, 1.0, 0.0)
-    assert float(J) == pytest.approx(Jo, rel=1e-12)
+    assert float(J.detach()) == pytest.approx(Jo, rel=1e-12)
     assert float(tau.grad) == pytest.approx(3 * dto, rel=1e-9)
     assert np.abs(uu.grad.numpy() - 3 * duo).max() <= 1e-9 * np.abs(duo).max()
-    assert np.abs(f.grad.numpy() - 3 * dfo).max() <= 1e-9 * np.abs(dfo).max()
+    assert f.grad.device == f.device
+    assert np.abs(f.grad.cpu().numpy() - 3 * dfo).max() <= 1e-9 * np.abs(dfo).max()
