@@ -30,7 +30,8 @@ struct AdjArgs {
     const uint8_t *tile_flag;  // per tile of the grid: 0 = every node's bits are 0 (or NULL)
     const double *u_row;
     double *du_acc;        // [ny] running dJ/du_in
-    double *dw_acc;        // [gridDim.x * gridDim.y] running per-block dJ/domega
+    double *dw_acc;        // [blocks * ADJ_WARPS] running per-warp dJ/domega: FP64, or a
+                           // float-float pair in the same 8 bytes below FP64 storage
     long long plane;
     int nx, ny, pitch;
     int in_window;
@@ -247,13 +248,15 @@ __global__ void __launch_bounds__(ADJ_THREADS, GBLBM_ADJ_MINB) k_adjoint_step(Ad
                 acc_add(dw, as_acc(adj_node<S>(a, idx, lt[r], g[r]), Acc()));
             } else {
                 if (x == 0 && !(nb[r] & 1)) {  // inlet: ft = feq(rho0, (u_in(y), 0))
-                    const double u = a.u_row[y];
-                    double s = 0.0;
+                    // in the compute type: FP64 instructions are slow on this
+                    // GPU even with one lane active, and this warp's siblings wait
+                    const T u = (T)a.u_row[y];
+                    const T r0 = param<T>(a.rho0, a.rho0_f);
+                    T s = T(0);
 #pragma unroll
                     for (int j = 0; j < 9; ++j)
-                        s += (double)lt[r][j] * wgt<double>(j) * a.rho0 *
-                             (3.0 * cx(j) + 9.0 * cx(j) * cx(j) * u - 3.0 * u);
-                    a.du_acc[y] += s;
+                        s += lt[r][j] * wgt<T>(j) * r0 * (T(3 * cx(j)) + T(9 * cx(j) * cx(j)) * u - T(3) * u);
+                    a.du_acc[y] += (double)s;
                 }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) lam[i * a.plane + idx] = T(0);
@@ -261,22 +264,25 @@ __global__ void __launch_bounds__(ADJ_THREADS, GBLBM_ADJ_MINB) k_adjoint_step(Ad
         }
     }
     // running sums of dJ/domega, one slot per warp (fixed order within the
-    // warp; float-float below FP64 storage, so that the per-node part stays
-    // off this GPU's few FP64 units, and no barrier between the warps)
+    // warp; float-float below FP64 storage, the running slot included, so
+    // that no FP64 instruction runs per step, and no barrier between warps)
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) acc_add(dw, shfl_down(dw, d));
     const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-    if ((threadIdx.x & 31) == 0)
-        a.dw_acc[((long long)blockIdx.y * gridDim.x + blockIdx.x) * ADJ_WARPS + warp] += acc_double(dw);
+    if ((threadIdx.x & 31) == 0) {
+        Acc *slot = (Acc *)a.dw_acc + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * ADJ_WARPS + warp;
+        acc_add(*slot, dw);
+    }
 }
 
 // Sum of n doubles in a fixed order (the final reduction): thread t of one
 // CTA adds slots t, t + 256, ... in turn, then the CTA's tree.
-__global__ void __launch_bounds__(256) k_sum_fixed(const double *__restrict__ v, long long n, double *__restrict__ out)
+template <typename A>
+__global__ void __launch_bounds__(256) k_sum_fixed(const A *__restrict__ v, long long n, double *__restrict__ out)
 {
     __shared__ double sh[256];
     double s = 0.0;
-    for (long long k = threadIdx.x; k < n; k += 256) s += v[k];
+    for (long long k = threadIdx.x; k < n; k += 256) s += acc_double(v[k]);
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int d = 128; d > 0; d >>= 1) {
@@ -350,9 +356,12 @@ cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sum_fixed(const double *v, long long n, double *out, cudaStream_t st)
+cudaError_t launch_sum_fixed(const double *v, long long n, double *out, bool ff_slots, cudaStream_t st)
 {
-    k_sum_fixed<<<1, 256, 0, st>>>(v, n, out);
+    if (ff_slots)
+        k_sum_fixed<ff><<<1, 256, 0, st>>>((const ff *)v, n, out);
+    else
+        k_sum_fixed<double><<<1, 256, 0, st>>>(v, n, out);
     return cudaGetLastError();
 }
 

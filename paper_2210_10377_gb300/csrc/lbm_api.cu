@@ -1318,7 +1318,7 @@ lbm_status lbm_adjoint(lbm_ctx *h, int steps, int window, double wx, double wy, 
             h->launches += 1;
         }
     }
-    if (e == cudaSuccess) e = launch_sum_fixed(dw_acc, nblk, dw_out, st);
+    if (e == cudaSuccess) e = launch_sum_fixed(dw_acc, nblk, dw_out, h->storage != LBM_F64, st);
     double dw = 0.0;
     std::vector<double> du(h->ny);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&dw, dw_out, sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -67,7 +67,7 @@ __device__ __forceinline__ void batch_tile(const BatchParams &p, int k)
         if constexpr (S == LBM_F64)
             set_relaxation_f64(a, m.omega);
         else
-            set_relaxation_f32(a, (float)m.omega);
+            set_relaxation_f32(a, m.omega_f);
         a.rho0 = p.rho0;
         a.gx = a.gy = 0.0;
         a.rho0_f = p.rho0_f;

@@ -51,7 +51,10 @@ __host__ __device__ constexpr int batch_rpt(int storage)
 // the constant bank with a block-uniform index).  Offsets are in units of 64
 // elements where the layout guarantees that alignment.
 struct BatchDomain {
-    double omega;     // 1/tau
+    union {
+        double omega;   // 1/tau (FP64 storage)
+        float omega_f;  // 1/tau rounded to FP32 (the other storages: no FP64 conversion per tile)
+    };
     int pop_off64;    // population arena offset / 64 (elements)
     int node_off64;   // neighbour-bit arena offset / 64
     int inlet_off64;  // inlet arena offset / 64 (elements)

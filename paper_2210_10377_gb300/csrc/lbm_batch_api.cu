@@ -25,12 +25,14 @@ using namespace gblbm;
 
 namespace {
 
-// Tiles of a launch ordered by code path or left in domain order, per storage
-// (a tuning knob; measured on the 256-domain recipe: path order takes FP16
-// deviations from 0.549 to 0.579 of the copy bandwidth and FP32 from 0.770
-// down to 0.739, so only FP16 uses it).
+// Tiles of a launch ordered by code path (1: interior, edge, body; 2: body,
+// edge, interior, so that the slower paths do not form the launch's tail) or
+// left in domain order (0), per storage (a tuning knob; measured on the
+// 256-domain recipe with 128-thread CTAs: FP16 deviations 0.480 in domain
+// order, 0.603 in order 1, 0.609 in order 2; FP32 dev 0.879 in domain order,
+// 0.857 in order 2, so only FP16 sorts).
 #ifndef GBLBM_BATCH_PATH_ORDER_F16
-#define GBLBM_BATCH_PATH_ORDER_F16 1
+#define GBLBM_BATCH_PATH_ORDER_F16 2
 #endif
 #ifndef GBLBM_BATCH_PATH_ORDER_F32
 #define GBLBM_BATCH_PATH_ORDER_F32 0
@@ -207,7 +209,10 @@ void make_params(const lbm_batch *b, int s, int src, int c, bool cv_only, bool t
     for (int d = d0; d < d1; ++d) {
         const Domain &m = b->dom[d];
         BatchDomain &q = p.dom[d - d0];
-        q.omega = 1.0 / m.tau;
+        if (b->storage == LBM_F64)
+            q.omega = 1.0 / m.tau;
+        else
+            q.omega_f = (float)(1.0 / m.tau);  // rounded as the single-domain handles round it
         q.pop_off64 = (int)(m.pop_off / 64);
         q.node_off64 = (int)(m.node_off / 64);
         q.inlet_off64 = (int)(m.inlet_off / 64);
@@ -682,9 +687,8 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
         // mostly run the same code, which keeps the instruction caches warm.
         // Any order gives the same bits: each tile writes its own nodes and
         // its own partial-sum slot.
-        const bool path_order =
-            b->storage == LBM_F16_DEV ? GBLBM_BATCH_PATH_ORDER_F16 != 0 : GBLBM_BATCH_PATH_ORDER_F32 != 0;
-        for (int c0 = 0; path_order && c0 < n; c0 += MAX_BATCH_DOMAINS) {
+        const int path_order = b->storage == LBM_F16_DEV ? GBLBM_BATCH_PATH_ORDER_F16 : GBLBM_BATCH_PATH_ORDER_F32;
+        for (int c0 = 0; path_order != 0 && c0 < n; c0 += MAX_BATCH_DOMAINS) {
             const int c1 = c0 + MAX_BATCH_DOMAINS < n ? c0 + MAX_BATCH_DOMAINS : n;
             const long long lo = b->dom[c0].tile_base[sh];
             const long long hi = c1 < n ? b->dom[c1].tile_base[sh] : (long long)chk.size();
@@ -695,8 +699,9 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
                 const bool edge_col = t.y == 0 || (t.y + 1) * tw >= m.nx - 1;
                 return edge_row || edge_col ? 1 : 0;
             };
-            std::stable_sort(chk.begin() + lo, chk.begin() + hi,
-                             [&](const int4 &u, const int4 &v) { return path(u) < path(v); });
+            std::stable_sort(chk.begin() + lo, chk.begin() + hi, [&](const int4 &u, const int4 &v) {
+                return path_order == 1 ? path(u) < path(v) : path(u) > path(v);
+            });
         }
         b->n_tiles[sh] = (long long)chk.size();
         b->n_cv_entries[sh] = (long long)chk_cv.size();

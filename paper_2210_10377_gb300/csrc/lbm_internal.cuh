@@ -255,7 +255,8 @@ cudaError_t launch_adjoint_step(int storage, const void *src, int precollision, 
                                 double *dw_acc, long long plane, int nx, int ny, int pitch,
                                 int in_window, double omega, double rho0, double obj_x,
                                 double obj_y, cudaStream_t st);
-cudaError_t launch_sum_fixed(const double *v, long long n, double *out, cudaStream_t st);
+// sum of n slots in a fixed order: FP64 values, or float-float pairs (ff_slots)
+cudaError_t launch_sum_fixed(const double *v, long long n, double *out, bool ff_slots, cudaStream_t st);
 // lambda (compute type, [9][ny][pitch]) -> dJ/df0 in FP64 [9][ny][nx] in device
 // memory, zero on solid nodes (mask) and in the inlet column
 cudaError_t launch_adjoint_df0(int storage, const void *lam, const uint8_t *mask, long long plane, int nx, int ny,

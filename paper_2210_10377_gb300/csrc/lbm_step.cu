@@ -55,14 +55,29 @@ template <> struct DirectMinBlocks<LBM_F16_DEV> {
 // min(x0 + 128, pitch) - 1) and starts on a 16-byte boundary (pitch is a
 // multiple of 64 elements); the halo rows and columns are the neighbouring
 // tiles' own rows.  A prefetch changes no value.
+// Tile row of the CTA row `by` of a full-grid launch.  The first and last
+// tile rows wrap in y and take the general path, several times slower a tile
+// than the interior path; dispatched last (in blockIdx order) they would form
+// the launch's tail, so they go first: the last row, then rows 0, 1, ...
+// (a tuning knob: 0 keeps blockIdx order).
+#ifndef GBLBM_WRAP_ROWS_FIRST
+#define GBLBM_WRAP_ROWS_FIRST 1
+#endif
+__device__ __forceinline__ int tile_row_of(int by, int tiles_y)
+{
+    if (!GBLBM_WRAP_ROWS_FIRST || tiles_y < 3) return by;
+    return by == 0 ? tiles_y - 1 : by - 1;
+}
+
 template <int S>
 __device__ __forceinline__ void prefetch_ahead(const StepArgs &a)
 {
     using E = typename Traits<S>::store_t;
     constexpr int TR = tile_rows(S);
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    const int ty = (int)blockIdx.y + a.pf_rows;
-    if (a.pf_rows <= 0 || t >= 9 * TR || ty >= (int)gridDim.y) return;
+    const int by = (int)blockIdx.y + a.pf_rows;
+    if (a.pf_rows <= 0 || t >= 9 * TR || by >= (int)gridDim.y) return;
+    const int ty = tile_row_of(by, (int)gridDim.y);
     const int y = ty * TR + t % TR;
     if (y >= a.ny) return;
     const int x0 = (int)blockIdx.x * TILE_X;
@@ -80,7 +95,10 @@ __global__ void __launch_bounds__((TILE_X / cols_per_thread(S)) * (tile_rows(S) 
     k_collide_stream(StepArgs a)
 {
     if constexpr (!MOMENTUM_ONLY) prefetch_ahead<S>(a);
-    const int tx = blockIdx.x + a.tile_off_x, ty = blockIdx.y + a.tile_off_y;
+    // a launch over a sub-rectangle of tiles (the momentum-only pass) keeps plain order
+    const int tx = blockIdx.x + a.tile_off_x;
+    const int ty = (MOMENTUM_ONLY || a.tile_off_y != 0) ? (int)blockIdx.y + a.tile_off_y
+                                                        : tile_row_of((int)blockIdx.y, (int)gridDim.y);
     const bool checked = a.precollision || a.tile_flag[(long long)ty * a.tiles_x + tx] != 0;
     collide_tile<S, MOMENTUM_ONLY, FORCE, TILE_X, tile_rows(S), direct_rpt(S)>(a, tx, ty, checked);
 }
