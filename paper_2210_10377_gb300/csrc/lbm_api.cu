@@ -624,7 +624,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     ALLOC(h->u_row, double *, sizeof(double) * ny);
     ALLOC(h->inlet, void *, 9 * (size_t)ny * h->elem);
     ALLOC(h->partials, double *, sizeof(double) * NBUF * CV_PARTIAL * h->n_cv_tiles);
-    ALLOC(h->link_partials, double *, sizeof(double) * LINK_PARTIAL * MAX_LINK_CTAS);
+    ALLOC(h->link_partials, double *, sizeof(double) * LINK_PARTIAL * MAX_LINK_CTAS * LINK_WARPS);
     ALLOC(h->ticket, unsigned int *, sizeof(unsigned int));
     ALLOC(h->carry, double *, sizeof(double) * 8);
     ALLOC(h->step_ctr, long long *, sizeof(long long));

@@ -50,6 +50,11 @@ __device__ __forceinline__ void acc_add(ff &a, ff b) { a = ff_add(a, b); }
 __device__ __forceinline__ double acc_double(double a) { return a; }
 __device__ __forceinline__ double acc_double(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ ff shfl_idx(ff v, int src)
+{
+    return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
 __device__ __forceinline__ ff shfl_down(ff v, int d)
 {
     return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};

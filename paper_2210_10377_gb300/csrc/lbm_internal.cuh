@@ -37,6 +37,7 @@ constexpr unsigned int WAIT_LIMIT = 1u << 22;  // default bound on every pipelin
 constexpr unsigned int DRAIN_LIMIT = 1u << 26;
 constexpr int PITCH_ALIGN = 64;
 constexpr int LINK_THREADS = 128;
+constexpr int LINK_WARPS = LINK_THREADS / 32;  // partial rows a link-kernel CTA writes
 // Threads of the batched link kernel's one CTA per domain (a tuning knob):
 // enough that a domain's links take one pass.
 #ifndef GBLBM_BATCH_LINK_THREADS

@@ -156,53 +156,70 @@ __device__ __forceinline__ void link_sums(const LinkArgs &a, long long k0, long 
     }
 }
 
-// Completes the force rows from the reduced sums d (one thread).  prev: the
-// row of step t-1, which receives DRTT(t-1) = J(t-1) - J(t) + (gained -
-// lost)(t-1) (Eq. rtt7, J(t-1) on the post-collision state, J(t) on the
-// pre-collision one); cur: the row of step t (A, B, A', defect), written and
-// the carry advanced unless drtt_only.  A null row pointer skips that row's
-// stores: the callers guard their row slots with plain branches, and no row
-// pointer may refer to a thread-local array (that form lost stores).
-__device__ __forceinline__ void finish_rows(const LinkArgs &a, const double (&d)[LINK_PARTIAL], long long t,
-                                            double *prev, double *cur, bool drtt_only)
+// Completes the force rows from the reduced sums d, one warp: lane k holds
+// d[k] (k < LINK_PARTIAL) and writes the outputs that need it, so that no
+// lane runs more than a few FP64 operations (one thread running them all in
+// turn took most of the kernel on this GPU's slow FP64 pipe).  prev: the row
+// of step t-1, which receives DRTT(t-1) = J(t-1) - J(t) + (gained - lost)(t-1)
+// (Eq. rtt7, J(t-1) on the post-collision state, J(t) on the pre-collision
+// one); cur: the row of step t (A, B, A', defect, SI), written and the carry
+// advanced unless drtt_only.  A null row pointer skips that row's stores.
+// Every lane reads the carry before any lane writes it.
+__device__ __forceinline__ void finish_rows_warp(const LinkArgs &a, double dk, long long t, double *prev,
+                                                 double *cur, bool drtt_only)
 {
-    if (prev && a.carry[4] != 0.0 && t >= 1) {
-        prev[4] = (a.carry[0] - d[6]) + a.carry[2];
-        prev[5] = (a.carry[1] - d[7]) + a.carry[3];
+    const int lane = threadIdx.x & 31;
+    const double d6 = shfl_idx(dk, 6), d7 = shfl_idx(dk, 7);
+    const double d8 = shfl_idx(dk, 8), d9 = shfl_idx(dk, 9);
+    const double c0 = a.carry[0], c1 = a.carry[1], c2 = a.carry[2], c3 = a.carry[3], c4 = a.carry[4];
+    __syncwarp();
+    if (prev && c4 != 0.0 && t >= 1) {
+        if (lane == 6) prev[4] = (c0 - d6) + c2;
+        if (lane == 7) prev[5] = (c1 - d7) + c3;
     }
     if (drtt_only) return;
     if (cur) {
-        cur[0] = d[0] + a.link_base[0];
-        cur[1] = d[1] + a.link_base[1];
-        cur[2] = d[2] + a.link_base[0];
-        cur[3] = d[3] + a.link_base[1];
-        cur[6] = d[4] + a.link_base[0];
-        cur[7] = d[5] + a.link_base[1];
-        cur[8] = d[6] - d[8];
-        cur[9] = d[7] - d[9];
-        cur[10] = d[12];
-        cur[11] = d[13];
+        switch (lane) {
+        case 0: cur[0] = dk + a.link_base[0]; break;
+        case 1: cur[1] = dk + a.link_base[1]; break;
+        case 2: cur[2] = dk + a.link_base[0]; break;
+        case 3: cur[3] = dk + a.link_base[1]; break;
+        case 4: cur[6] = dk + a.link_base[0]; break;
+        case 5: cur[7] = dk + a.link_base[1]; break;
+        case 6: cur[8] = dk - d8; break;
+        case 7: cur[9] = dk - d9; break;
+        case 12: cur[10] = dk; break;
+        case 13: cur[11] = dk; break;
+        default: break;
+        }
     }
-    a.carry[0] = d[8];
-    a.carry[1] = d[9];
-    a.carry[2] = d[10] + a.flux_base[0];
-    a.carry[3] = d[11] + a.flux_base[1];
-    a.carry[4] = 1.0;
+    switch (lane) {
+    case 8: a.carry[0] = dk; break;
+    case 9: a.carry[1] = dk; break;
+    case 10: a.carry[2] = dk + a.flux_base[0]; break;
+    case 11: a.carry[3] = dk + a.flux_base[1]; break;
+    case 14: a.carry[4] = 1.0; break;
+    default: break;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Link force + finalisation of one domain.  n_ctas CTAs of LINK_THREADS
 // threads share the links (contiguous chunks) and the control-volume
 // partials; each writes one partial row.  The last CTA to finish (atomic
-// ticket) sums the rows in slot order, so the result does not depend on which
-// CTA finishes last, and completes the step's series row and the DRTT of the
-// previous step.
+// ticket, one per warp) sums the warps' rows in a fixed order, so the result
+// does not depend on which warp finishes last, and its lanes complete the
+// step's series row and the DRTT of the previous step.
 // Series row t: A(2) B(2) DRTT(2) A'(2) defect(2) SI(2), where defect is the
 // collision's momentum defect inside the box, J_pre(t) - J_post(t).
 // For deviation storage the momentum of the base w_i rho0 over the links and
 // over the box-surface crossings is a fixed geometric sum (link_base,
 // flux_base, from the host) added at the end.
 // ---------------------------------------------------------------------------
+// Load each thread's first control-volume row before the link loop (a tuning knob).
+#ifndef GBLBM_LINK_EARLY
+#define GBLBM_LINK_EARLY 1
+#endif
 template <int S>
 __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
 {
@@ -216,63 +233,76 @@ __global__ void __launch_bounds__(LINK_THREADS) k_link_force(LinkArgs a)
         const int per_p = (a.n_partials + gridDim.x - 1) / gridDim.x;
         const int p0 = per_p * blockIdx.x;
         const int p1 = p0 + per_p < a.n_partials ? p0 + per_p : a.n_partials;
-        link_sums<S, LINK_THREADS, false>(a, k0, k1 > k0 ? k1 : k0, p0, p1 > p0 ? p1 : p0, v);
+        link_sums<S, LINK_THREADS, GBLBM_LINK_EARLY != 0>(a, k0, k1 > k0 ? k1 : k0, p0, p1 > p0 ? p1 : p0, v);
     }
-    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(v);
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        A *row = (A *)a.link_partials + LINK_PARTIAL * (long long)blockIdx.x;
+    // each warp reduces its sums and writes them as one row (slot: CTA, warp);
+    // no block barrier, and the last warp to take a ticket completes the step
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+        for (int k = 0; k < LINK_PARTIAL; ++k) acc_add(v[k], shfl_down(v[k], d));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rows = (int)gridDim.x * LINK_WARPS;
+    unsigned int ticket = 0;
+    if (lane == 0) {
+        A *row = (A *)a.link_partials + LINK_PARTIAL * ((long long)blockIdx.x * LINK_WARPS + warp);
 #pragma unroll
         for (int k = 0; k < LINK_PARTIAL; ++k) row[k] = v[k];
         __threadfence();
-        const unsigned int ticket = atomicAdd(a.ticket, 1u);
-        last = ticket == gridDim.x - 1;
+        ticket = atomicAdd(a.ticket, 1u);
     }
-    __syncthreads();
-    if (!last) return;
+    ticket = __shfl_sync(0xffffffffu, ticket, 0);
+    if (ticket != (unsigned int)rows - 1) return;
     __threadfence();
-    A w[LINK_PARTIAL];
-#pragma unroll
-    for (int k = 0; k < LINK_PARTIAL; ++k) acc_zero(w[k]);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += LINK_THREADS) {
-        const volatile A *row = (const volatile A *)a.link_partials + LINK_PARTIAL * (long long)b;
-#pragma unroll
-        for (int k = 0; k < LINK_PARTIAL; ++k) {
+    // lane k and lane 16 + k add sum k over the first and the second half of
+    // the rows in slot order, then lane k adds the two halves.  The rows are
+    // read from L2 (ld.global.cg), where the other warps' stores and fences
+    // put them: an SM's L1 is not kept coherent within a launch.
+    static_assert(LINK_PARTIAL <= 16, "two lanes per sum");
+    const int k = lane & 15, half = (rows + 1) / 2;
+    const int r0 = lane < 16 ? 0 : half, r1 = lane < 16 ? half : rows;
+    A mine;
+    acc_zero(mine);
+    if (k < LINK_PARTIAL) {
+        const A *col = (const A *)a.link_partials + k;
+        for (int b = r0; b < r1; ++b) {
             A r;
             if constexpr (S == LBM_F64)
-                r = row[k];
+                r = __ldcg(col + LINK_PARTIAL * (long long)b);
             else
-                r = {row[k].hi, row[k].lo};
-            acc_add(w[k], r);
+                r = {__ldcg(&col[LINK_PARTIAL * (long long)b].hi), __ldcg(&col[LINK_PARTIAL * (long long)b].lo)};
+            acc_add(mine, r);
         }
     }
-    block_reduce<A, LINK_PARTIAL, LINK_THREADS>(w);
-    if (threadIdx.x == 0) {
+    {
+        const A upper = shfl_down(mine, 16);
+        if (lane < 16) acc_add(mine, upper);
+    }
+    const double dk = acc_double(mine);
+    const long long t = *a.step_ctr;
+    // Series slot of a step: the step itself, or its parity when only the
+    // last two rows are kept.  A slot beyond the buffer (an internal
+    // invariant: the host grows the series before every launch) is not
+    // written and raises status bit 4.
+    const bool keep_all = a.record_series != 0;
+    const long long kp = keep_all ? t - 1 : ((t - 1) & 1), kc = keep_all ? t : (t & 1);
+    double *prev = nullptr, *cur = nullptr;
+    if (t >= 1 && a.carry[4] != 0.0) {
+        if (kp < a.series_rows)
+            prev = a.series + SERIES_ROW * kp;
+        else if (lane == 0)
+            atomicOr(a.status, 4);
+    }
+    if (!a.drtt_only) {
+        if (kc < a.series_rows)
+            cur = a.series + SERIES_ROW * kc;
+        else if (lane == 0)
+            atomicOr(a.status, 4);
+    }
+    finish_rows_warp(a, dk, t, prev, cur, a.drtt_only != 0);
+    __syncwarp();
+    if (lane == 0) {
         *a.ticket = 0u;
-        double d[LINK_PARTIAL];
-#pragma unroll
-        for (int k = 0; k < LINK_PARTIAL; ++k) d[k] = acc_double(w[k]);
-        const long long t = *a.step_ctr;
-        // Series slot of a step: the step itself, or its parity when only the
-        // last two rows are kept.  A slot beyond the buffer (an internal
-        // invariant: the host grows the series before every launch) is not
-        // written and raises status bit 4.
-        const bool keep_all = a.record_series != 0;
-        const long long kp = keep_all ? t - 1 : ((t - 1) & 1), kc = keep_all ? t : (t & 1);
-        double *prev = nullptr, *cur = nullptr;
-        if (t >= 1 && a.carry[4] != 0.0) {
-            if (kp < a.series_rows)
-                prev = a.series + SERIES_ROW * kp;
-            else
-                atomicOr(a.status, 4);
-        }
-        if (!a.drtt_only) {
-            if (kc < a.series_rows)
-                cur = a.series + SERIES_ROW * kc;
-            else
-                atomicOr(a.status, 4);
-        }
-        finish_rows(a, d, t, prev, cur, a.drtt_only != 0);
         if (!a.drtt_only) *a.step_ctr = t + 1;
     }
 }
@@ -324,10 +354,18 @@ __global__ void __launch_bounds__(BATCH_LINK_THREADS) k_link_force_batch(BatchLi
     A v[LINK_PARTIAL];
     link_sums<S, BATCH_LINK_THREADS, true>(la, 0, b.drtt_only ? 0 : la.nlinks, 0, la.n_partials, v);
     block_reduce<A, LINK_PARTIAL, BATCH_LINK_THREADS>(v);
-    if (threadIdx.x == 0) {
-        double d[LINK_PARTIAL];
+    if (threadIdx.x < 32) {
+        // warp 0 finishes the domain's rows, lane k with total k (thread 0
+        // holds the totals after the block reduction)
+        const int lane = threadIdx.x;
+        A mine;
+        acc_zero(mine);
 #pragma unroll
-        for (int k = 0; k < LINK_PARTIAL; ++k) d[k] = acc_double(v[k]);
+        for (int k = 0; k < LINK_PARTIAL; ++k) {
+            const A tk = shfl_idx(v[k], 0);
+            if (lane == k) mine = tk;
+        }
+        const double dk = acc_double(mine);
         const long long t = t_sh;
         const long long kp = b.keep_all ? t - 1 : ((t - 1) & 1), kc = b.keep_all ? t : (t & 1);
         const long long stride = (long long)b.n_domains * SERIES_ROW;
@@ -335,21 +373,24 @@ __global__ void __launch_bounds__(BATCH_LINK_THREADS) k_link_force_batch(BatchLi
         if (t >= 1 && la.carry[4] != 0.0) {
             if (kp < b.series_rows)
                 prev = b.series + stride * kp + SERIES_ROW * (long long)blockIdx.x;
-            else
+            else if (lane == 0)
                 atomicOr(b.status, 4);
         }
         if (!b.drtt_only) {
             if (kc < b.series_rows)
                 cur = b.series + stride * kc + SERIES_ROW * (long long)blockIdx.x;
-            else
+            else if (lane == 0)
                 atomicOr(b.status, 4);
         }
-        finish_rows(la, d, t, prev, cur, b.drtt_only != 0);
+        finish_rows_warp(la, dk, t, prev, cur, b.drtt_only != 0);
         __threadfence();
-        const unsigned int ticket = atomicAdd(b.ticket, 1u);
-        if (ticket == gridDim.x - 1) {
-            *b.ticket = 0u;
-            if (!b.drtt_only) *b.step_ctr = t + 1;
+        __syncwarp();
+        if (lane == 0) {
+            const unsigned int ticket = atomicAdd(b.ticket, 1u);
+            if (ticket == gridDim.x - 1) {
+                *b.ticket = 0u;
+                if (!b.drtt_only) *b.step_ctr = t + 1;
+            }
         }
     }
 }
