@@ -120,6 +120,33 @@ def test_f64_ragged_random_bodies(gb, kind):
         assert np.abs(gx - ox).max() <= 1e-11 and np.abs(gy - oy).max() <= 1e-11, s
 
 
+def test_f64_link_kernel_at_its_cta_cap(gb):
+    # ~35 k links: the link kernel runs its maximum of 148 CTAs (592 warp rows,
+    # two lanes per sum in its completion); eager steps, graphs and the held
+    # link kernels at every chunk boundary
+    nx, ny = 640, 320
+    m = inputs.random_blobs_mask(nx, ny, 900, seed=77, max_radius=4.0, margin_x=3)
+    assert len(oracle.links(m, False)) > 148 * 128
+    f0 = inputs.random_populations(nx, ny, seed=78, lo=0.03, hi=0.12)
+    sim, lat = run_pair(gb, m, 0.6, 0.04, 40, kind=oracle.BC_CHANNEL, f0=f0, chunks=[1, 2, 18, 19])
+    f = sim.populations()
+    assert np.abs(lat.populations() - f).max() <= 1e-12
+    # DRTT differences J(t) and J(t+1), sums of c_i f_i over the box (here
+    # nearly the whole grid, ~1.8 M terms of a random state) that the two
+    # sides add in different orders: its bar is the error of two such sums,
+    # 2 eps log2(n) sum|c_i f_i| (eps = 2^-53), not a share of the force
+    x0, x1, y0, y1 = lat.control_volume()
+    box = f[:, y0:y1 + 1, x0:x1 + 1]
+    drtt_bar = 2 * 2.0 ** -53 * np.ceil(np.log2(box.size)) * np.sqrt(2.0) * np.abs(box).sum()
+    for s in SCHEMES:
+        ox, oy = sim.force_series(ORACLE_SCHEME[s])
+        gx, gy = lat.force_series(s)
+        sc = max(np.abs(ox).max(), np.abs(oy).max())
+        bar = max(1e-12 * sc, drtt_bar) if s == "DRTT" else 1e-12 * sc
+        ex, ey = np.abs(gx - ox).max(), np.abs(gy - oy).max()
+        assert ex <= bar and ey <= bar, (s, ex, ey, bar)
+
+
 def test_f64_body_force_and_explicit_cv(gb):
     nx, ny = 70, 24
     m = np.zeros((ny, nx), np.uint8)
