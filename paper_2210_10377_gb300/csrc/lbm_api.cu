@@ -37,6 +37,10 @@ static_assert(GRAPH_STEPS % NBUF == 0 && GRAPH_STEPS >= NBUF, "GRAPH_STEPS: a mu
 #define GBLBM_ADJ_KEEP_SHARE 0.6
 #endif
 constexpr double ADJ_KEEP_SHARE = GBLBM_ADJ_KEEP_SHARE;
+// Dispatch the tile rows that hold bounce-back tiles first (a tuning knob).
+#ifndef GBLBM_BODY_ROWS_FIRST
+#define GBLBM_BODY_ROWS_FIRST 1
+#endif
 constexpr int TIMING_BATCH = 64;
 
 }  // namespace
@@ -62,6 +66,7 @@ struct lbm_ctx {
     bool tmap_ok = false;
     int use_bulk = 0, sm_count = 1;
     int pf_rows = 0;                                     // L2 prefetch distance of the direct kernel
+    int first_r0 = 1, first_r1 = 0;                      // tile rows holding bounce-back tiles (none: r0 > r1)
     unsigned int wait_limit = WAIT_LIMIT;                // polls of each staged-kernel pipeline wait
     int cur = 0;                 // buffer holding the latest state
     cudaStream_t side = nullptr; // link kernels
@@ -232,6 +237,8 @@ StepArgs step_args(lbm_ctx *h, int src, int dst, int precollision)
     a.use_bulk = h->use_bulk;
     a.sm_count = h->sm_count;
     a.pf_rows = h->pf_rows;
+    a.first_r0 = h->first_r0;
+    a.first_r1 = h->first_r1;
     a.wait_limit = h->wait_limit;
     return a;
 }
@@ -651,6 +658,8 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     CKC(launch_tile_flags(h->nbits, nx, ny, h->pitch, periodic, h->tile_flag, h->tiles_x, h->tiles_y,
                           TILE_X, tile_rows(h->storage), s),
         "tile flags");
+    std::vector<uint8_t> flags((size_t)h->tiles_x * h->tiles_y);
+    CKC(cudaMemcpyAsync(flags.data(), h->tile_flag, flags.size(), cudaMemcpyDeviceToHost, s), "D2H tile flags");
     // link list: count, scan, scatter
     const int nb = link_blocks(nx, ny);
     int *blk = nullptr;
@@ -667,6 +676,20 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if (le == cudaSuccess) le = cudaMemcpyAsync(&total, total_d, sizeof(total), cudaMemcpyDeviceToHost, s);
     if (le == cudaSuccess) le = cudaStreamSynchronize(s);
     if (le == cudaSuccess) {
+        // the tile rows holding bounce-back tiles run first in each step (a
+        // body's rows; rows spread over more than half the grid keep their order)
+        int r0 = h->tiles_y, r1 = -1;
+        for (int ty = 0; ty < h->tiles_y; ++ty)
+            for (int tx = 0; tx < h->tiles_x; ++tx)
+                if (flags[(size_t)ty * h->tiles_x + tx]) {
+                    r0 = ty < r0 ? ty : r0;
+                    r1 = ty > r1 ? ty : r1;
+                    break;
+                }
+        if (GBLBM_BODY_ROWS_FIRST && r1 >= r0 && 2 * (r1 - r0 + 1) <= h->tiles_y) {
+            h->first_r0 = r0;
+            h->first_r1 = r1;
+        }
         h->nlinks = total;
         {
             long long work = total > h->n_cv_tiles ? total : h->n_cv_tiles;

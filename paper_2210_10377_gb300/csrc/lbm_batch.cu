@@ -64,6 +64,8 @@ __device__ __forceinline__ void batch_tile(const BatchParams &p, int k)
         a.tiles_x = m.tiles_x;
         a.tile_off_x = a.tile_off_y = 0;
         a.pf_rows = 0;
+        a.first_r0 = 1;
+        a.first_r1 = 0;
         if constexpr (S == LBM_F64)
             set_relaxation_f64(a, m.omega);
         else

@@ -149,6 +149,7 @@ struct StepArgs {
     int use_bulk;            // staged (TMA) kernel allowed (channel set-up, pulled state)
     int sm_count;            // persistent grid size of the staged kernel
     int pf_rows;             // L2 prefetch distance of the direct kernel in tile rows (0: off)
+    int first_r0, first_r1;  // tile rows with bounce-back tiles, dispatched first (r0 > r1: none)
     unsigned int wait_limit; // polls of each pipeline wait of the staged kernel (WAIT_LIMIT)
 };
 

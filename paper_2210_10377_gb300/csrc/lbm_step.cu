@@ -55,18 +55,27 @@ template <> struct DirectMinBlocks<LBM_F16_DEV> {
 // min(x0 + 128, pitch) - 1) and starts on a 16-byte boundary (pitch is a
 // multiple of 64 elements); the halo rows and columns are the neighbouring
 // tiles' own rows.  A prefetch changes no value.
-// Tile row of the CTA row `by` of a full-grid launch.  The first and last
-// tile rows wrap in y and take the general path, several times slower a tile
-// than the interior path; dispatched last (in blockIdx order) they would form
-// the launch's tail, so they go first: the last row, then rows 0, 1, ...
-// (a tuning knob: 0 keeps blockIdx order).
+// Tile row of the CTA row `by` of a full-grid launch.  Tiles that take the
+// slower paths run first instead of forming the launch's tail: the rows
+// [r0, r1] that hold bounce-back tiles (next to a body; several times an
+// interior tile's time), then the last and the first tile row, which wrap in
+// y and take the general path, then the other rows in order.  The mapping is
+// arithmetic, so the L2 prefetch of the tile pf_rows CTA rows ahead finds its
+// target without a load (a tuning knob: 0 keeps blockIdx order).
 #ifndef GBLBM_WRAP_ROWS_FIRST
 #define GBLBM_WRAP_ROWS_FIRST 1
 #endif
-__device__ __forceinline__ int tile_row_of(int by, int tiles_y)
+__device__ __forceinline__ int tile_row_of(int by, int tiles_y, int r0, int r1)
 {
     if (!GBLBM_WRAP_ROWS_FIRST || tiles_y < 3) return by;
-    return by == 0 ? tiles_y - 1 : by - 1;
+    // the body's rows strictly inside (the wrap rows come next in any case)
+    const int b0 = r0 < 1 ? 1 : r0, b1 = r1 > tiles_y - 2 ? tiles_y - 2 : r1;
+    const int nb = b1 >= b0 ? b1 - b0 + 1 : 0;
+    if (by < nb) return b0 + by;
+    if (by == nb) return tiles_y - 1;
+    if (by == nb + 1) return 0;
+    const int k = by - nb - 2;  // among the rows 1 .. tiles_y - 2 outside [b0, b1], in order
+    return (nb == 0 || 1 + k < b0) ? 1 + k : 1 + k + nb;
 }
 
 template <int S>
@@ -77,7 +86,7 @@ __device__ __forceinline__ void prefetch_ahead(const StepArgs &a)
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
     const int by = (int)blockIdx.y + a.pf_rows;
     if (a.pf_rows <= 0 || t >= 9 * TR || by >= (int)gridDim.y) return;
-    const int ty = tile_row_of(by, (int)gridDim.y);
+    const int ty = tile_row_of(by, (int)gridDim.y, a.first_r0, a.first_r1);
     const int y = ty * TR + t % TR;
     if (y >= a.ny) return;
     const int x0 = (int)blockIdx.x * TILE_X;
@@ -98,7 +107,8 @@ __global__ void __launch_bounds__((TILE_X / cols_per_thread(S)) * (tile_rows(S) 
     // a launch over a sub-rectangle of tiles (the momentum-only pass) keeps plain order
     const int tx = blockIdx.x + a.tile_off_x;
     const int ty = (MOMENTUM_ONLY || a.tile_off_y != 0) ? (int)blockIdx.y + a.tile_off_y
-                                                        : tile_row_of((int)blockIdx.y, (int)gridDim.y);
+                                                        : tile_row_of((int)blockIdx.y, (int)gridDim.y,
+                                                                      a.first_r0, a.first_r1);
     const bool checked = a.precollision || a.tile_flag[(long long)ty * a.tiles_x + tx] != 0;
     collide_tile<S, MOMENTUM_ONLY, FORCE, TILE_X, tile_rows(S), direct_rpt(S)>(a, tx, ty, checked);
 }
