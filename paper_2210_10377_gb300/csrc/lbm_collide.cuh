@@ -424,13 +424,31 @@ __device__ __forceinline__ void column_update_interior(const StepArgs &a, int x,
         for (int i = 0; i < 9; ++i)
             f[r][i] = to_comp(b[r * pitch + i * plane - cy(i) * pitch - cx(i)]);
     constexpr bool PAIRS = sizeof(T) == 4 && RPT % 2 == 0 && !MOMENTUM_ONLY;
+    // FP32 storages: the inlet lane runs the same instructions as its warp on
+    // its (unused) pulls and then takes the inlet's values, so that its warp
+    // does not split into two paths (its collision raises no instability
+    // flag).  FP16 deviations reach this form only off their column-pair path
+    // and keep the inlet apart: on their tighter register budget the inlet in
+    // the pair paths cost them 4-15 % (measured).
+    constexpr bool INLET_IN_PAIRS = S != LBM_F16_DEV;
     if constexpr (PAIRS) {
-      if (!inlet) {
+      if (INLET_IN_PAIRS || !inlet) {
         // two rows at a time in packed FP32 pairs (identical bits to one node at a time)
 #pragma unroll
         for (int r = 0; r < RPT; r += 2) {
             ST out0[9], out1[9];
-            collide_pair<S, FORCE>(a, f[r], f[r + 1], out0, out1, bad);
+            bool bad2 = false;
+            collide_pair<S, FORCE>(a, f[r], f[r + 1], out0, out1, bad2);
+            if (INLET_IN_PAIRS && inlet) {
+                const ST *in = (const ST *)a.inlet;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    out0[i] = in[i * a.ny + y0 + r];
+                    out1[i] = in[i * a.ny + y0 + r + 1];
+                }
+            } else if (bad2) {
+                bad = true;
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 o[r * pitch + i * plane] = out0[i];
