@@ -731,19 +731,26 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
 
 namespace {
 
+// Clears the status words for the steps about to be queued, unless the last
+// settle already did: status[0] = 0 (no flag), status[1] = 0x7f7f7f7f (no bad
+// step yet).
+lbm_status arm_status(lbm_ctx *h)
+{
+    if (h->status_armed) return LBM_OK;
+    CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
+    CK(h, cudaMemsetAsync(h->status + 1, 0x7f, sizeof(int), h->stream), "status reset");
+    h->status_armed = true;
+    return LBM_OK;
+}
+
 // Queues n steps on the handle's stream without waiting for them.  The
 // status words are cleared before the first queued step after a settle and
 // then collect the flags of every step until the next settle.
 lbm_status queue_steps(lbm_ctx *h, int n)
 {
     lbm_status st = ensure_series(h, h->t + n);
+    if (st == LBM_OK) st = arm_status(h);
     if (st != LBM_OK) return st;
-    if (!h->status_armed) {
-        // status[0] = 0 (no flag), status[1] = 0x7f7f7f7f (no bad step yet)
-        CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
-        CK(h, cudaMemsetAsync(h->status + 1, 0x7f, sizeof(int), h->stream), "status reset");
-        h->status_armed = true;
-    }
     if (h->timing && (int)h->events.size() < 3 * TIMING_BATCH) {
         h->events.resize(3 * TIMING_BATCH, nullptr);
         for (auto &e : h->events)
@@ -804,12 +811,8 @@ lbm_status queue_steps(lbm_ctx *h, int n)
 lbm_status queue_steps_keep(lbm_ctx *h, int n, char *slots, size_t stride)
 {
     lbm_status st = ensure_series(h, h->t + n);
+    if (st == LBM_OK) st = arm_status(h);
     if (st != LBM_OK) return st;
-    if (!h->status_armed) {
-        CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
-        CK(h, cudaMemsetAsync(h->status + 1, 0x7f, sizeof(int), h->stream), "status reset");
-        h->status_armed = true;
-    }
     void *orig[NBUF];
     for (int b = 0; b < NBUF; ++b) orig[b] = h->pop[b];
     const int bulk = h->use_bulk;
