@@ -361,7 +361,14 @@ class Lattice:
         _check(lib().lbm_control_volume(self._h, cv), self._h)
         return list(cv)
 
-    def adjoint(self, steps, window, wx=1.0, wy=0.0, checkpoint_every=0, want_df0=True, df0_device=False):
+    def set_adjoint_budget(self, nbytes):
+        """Device memory lbm_adjoint may fill with kept states (lbm_set_adjoint_budget;
+        0: 60 % of the free memory).  adjoint() sets it from torch's view of the
+        memory unless keep_budget=True is passed."""
+        _check(lib().lbm_set_adjoint_budget(self._h, float(nbytes)), self._h)
+
+    def adjoint(self, steps, window, wx=1.0, wy=0.0, checkpoint_every=0, want_df0=True, df0_device=False,
+                keep_budget=False):
         """Run `steps` steps and return (J, dJ/dtau, dJ/du_in[ny], dJ/df0[9][ny][nx] or
         None) for J = the window-averaged wx Fx + wy Fy of algorithm B.
         df0_device: dJ/df0 as a float64 CUDA tensor on the handle's device,
@@ -369,7 +376,7 @@ class Lattice:
         J, dtau = C.c_double(), C.c_double()
         du = np.zeros(self.ny)
         df0, ptr = None, None
-        if checkpoint_every <= 0 and self._alloc is not None:
+        if checkpoint_every <= 0 and self._alloc is not None and not keep_budget:
             # what torch can provide: the free memory and its own unused cache
             import torch
             free, _ = torch.cuda.mem_get_info(self.device)

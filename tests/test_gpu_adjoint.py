@@ -71,6 +71,32 @@ def test_kept_states_give_the_bits_of_recomputed_states(gb, storage):
     assert np.array_equal(pops[0], pops[1])
 
 
+def test_adjoint_budget_changes_the_plan_not_the_bits(gb):
+    # a budget below the fixed reserve keeps no state (every segment is
+    # recomputed), a budget of the reserve plus ~40 states keeps part of the
+    # run, the default keeps all of this small case: the same bits each time
+    m, u, f0 = small_case(17)
+    nx, ny = m.shape[1], m.shape[0]
+    state = 9 * ny * 64 * 8  # FP64 [9][ny][pitch 64]
+    reserve = 2 * state + 72 * nx * ny + 2 ** 30
+    outs = []
+    for budget in (None, 1.0, reserve + 40.5 * state):
+        lat = gb.Lattice(m, 0.7, u, storage="f64")
+        lat.set_populations(f0)
+        if budget is not None:
+            lat.set_adjoint_budget(budget)
+        outs.append(lat.adjoint(90, 40, 0.5, 0.5, keep_budget=budget is not None))
+        lat.close()
+    ref = gpu_adjoint(gb, m, 0.7, u, f0, 90, 40, 0.5, 0.5, "f64", 7)
+    for J, dt, du, df in outs:
+        assert J == ref[0] and dt == ref[1]
+        assert np.array_equal(du, ref[2]) and np.array_equal(df, ref[3])
+    lat = gb.Lattice(m, 0.7, u, storage="f64")
+    with pytest.raises(gb.LbmError):
+        lat.set_adjoint_budget(-1.0)
+    lat.close()
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32dev"])
 def test_df0_in_device_memory_equals_the_host_copy(gb, storage):
     # dJ/df0 written in place into a CUDA tensor equals the host read-back bit
