@@ -537,8 +537,6 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     h->g[0] = bc.body_force[0];
     h->g[1] = bc.body_force[1];
     memcpy(h->cv, cv, sizeof(cv));
-    if (bc.storage == LBM_F32_DEV || bc.storage == LBM_F16_DEV)
-        base_sums(mask, nx, ny, periodic, cv, bc.rho0, h->link_base, h->flux_base);
     h->record_series = bc.record_series ? 1 : 0;
     h->use_bulk = bc.kernel == 1;
     {
@@ -674,6 +672,10 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if (le == cudaSuccess) le = launch_scan_blocks(blk, nb, total_d, s);
     long long total = 0;
     if (le == cudaSuccess) le = cudaMemcpyAsync(&total, total_d, sizeof(total), cudaMemcpyDeviceToHost, s);
+    // the host's scan of the mask for the deviation base sums runs while the
+    // device builds the node bits and counts the links
+    if (bc.storage == LBM_F32_DEV || bc.storage == LBM_F16_DEV)
+        base_sums(mask, nx, ny, periodic, h->cv, bc.rho0, h->link_base, h->flux_base);
     if (le == cudaSuccess) le = cudaStreamSynchronize(s);
     if (le == cudaSuccess) {
         // the tile rows holding bounce-back tiles run first in each step (a
