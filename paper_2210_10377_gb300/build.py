@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             raise RuntimeError("nvcc failed on " + cmd[-3])
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp], check=True)
+        subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", *objs, "-lpthread", "-o", tmp], check=True)
         os.replace(tmp, LIB)
     return LIB
 

@@ -513,9 +513,14 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     if ((bc.alloc == nullptr) != (bc.free == nullptr))
         return set_err(nullptr, LBM_EINVAL, "alloc and free must be given together");
     const int periodic = bc.kind == LBM_BC_PERIODIC;
+    // the mask's solid nodes, scanned once for the default box and the base sums
+    std::vector<long long> solids;
+    const bool need_solids = bc.cv[0] < 0 || bc.storage == LBM_F32_DEV || bc.storage == LBM_F16_DEV;
+    if (mask && need_solids && nx > 0 && ny > 0 && (long long)nx * ny * 8 < (1LL << 31))
+        solids = solid_nodes(mask, nx, ny);
     int cv[4];
     {
-        const std::string why = check_domain(mask, nx, ny, tau, u_in, n_u_in, periodic, bc.cv, cv);
+        const std::string why = check_domain(mask, nx, ny, tau, u_in, n_u_in, periodic, bc.cv, cv, &solids);
         if (!why.empty()) return set_err(nullptr, LBM_EINVAL, "%s", why.c_str());
     }
     int ndev = 0;
@@ -675,7 +680,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
     // the host's scan of the mask for the deviation base sums runs while the
     // device builds the node bits and counts the links
     if (bc.storage == LBM_F32_DEV || bc.storage == LBM_F16_DEV)
-        base_sums(mask, nx, ny, periodic, h->cv, bc.rho0, h->link_base, h->flux_base);
+        base_sums(mask, nx, ny, periodic, h->cv, bc.rho0, h->link_base, h->flux_base, &solids);
     if (le == cudaSuccess) le = cudaStreamSynchronize(s);
     if (le == cudaSuccess) {
         // the tile rows holding bounce-back tiles run first in each step (a

@@ -2,6 +2,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <thread>
 #include <vector>
 
 #include "gblbm.h"
@@ -20,31 +22,62 @@ size_t storage_bytes(int storage)
 
 namespace {
 
-// Row-major indices of the solid (nonzero) mask bytes.  Masks are mostly
-// fluid, so eight bytes are tested at a time and zero words skipped.
-std::vector<long long> solid_nodes(const uint8_t *mask, int nx, int ny)
+// Solid indices in [lo, hi): eight bytes are tested at a time (masks are
+// mostly fluid) and zero words skipped.  lo is a multiple of 8.
+void scan_solids(const uint8_t *mask, size_t lo, size_t hi, std::vector<long long> &out)
 {
-    std::vector<long long> out;
-    const size_t n = (size_t)nx * ny;
-    size_t i = 0;
-    for (; i + 8 <= n; i += 8) {
+    size_t i = lo;
+    for (; i + 8 <= hi; i += 8) {
         uint64_t w;
         memcpy(&w, mask + i, 8);
         if (w == 0) continue;
         for (size_t k = i; k < i + 8; ++k)
             if (mask[k]) out.push_back((long long)k);
     }
-    for (; i < n; ++i)
+    for (; i < hi; ++i)
         if (mask[i]) out.push_back((long long)i);
-    return out;
 }
 
 }  // namespace
 
-void auto_cv(const uint8_t *mask, int nx, int ny, int periodic, int *cv)
+std::vector<long long> solid_nodes(const uint8_t *mask, int nx, int ny)
 {
+    const size_t n = (size_t)nx * ny;
+    std::vector<long long> out;
+    unsigned nt = 1;
+    if (n >= ((size_t)1 << 22)) {
+        const unsigned hc = std::thread::hardware_concurrency();
+        nt = hc < 2 ? 1 : (hc < 8 ? hc : 8);
+    }
+    if (nt > 1) {
+        try {
+            const size_t chunk = (n / nt + 7) & ~(size_t)7;
+            std::vector<std::vector<long long>> parts(nt);
+            std::vector<std::thread> th;
+            for (unsigned k = 0; k < nt; ++k) {
+                const size_t lo = k * chunk, hi = lo + chunk < n ? lo + chunk : n;
+                if (lo < hi) th.emplace_back(scan_solids, mask, lo, hi, std::ref(parts[k]));
+            }
+            for (auto &t : th) t.join();
+            for (auto &p : parts) out.insert(out.end(), p.begin(), p.end());
+            return out;
+        } catch (...) {
+            out.clear();  // no threads to be had: one scan here
+        }
+    }
+    scan_solids(mask, 0, n, out);
+    return out;
+}
+
+void auto_cv(const uint8_t *mask, int nx, int ny, int periodic, int *cv, const std::vector<long long> *solids)
+{
+    std::vector<long long> own;
+    if (!solids) {
+        own = solid_nodes(mask, nx, ny);
+        solids = &own;
+    }
     int xmin = nx, xmax = -1, ymin = ny, ymax = -1;
-    for (long long k : solid_nodes(mask, nx, ny)) {
+    for (long long k : *solids) {
         const int x = (int)(k % nx), y = (int)(k / nx);
         xmin = x < xmin ? x : xmin;
         xmax = x > xmax ? x : xmax;
@@ -84,8 +117,13 @@ void auto_cv(const uint8_t *mask, int nx, int ny, int periodic, int *cv)
 // bounced ft_i.  Links are enumerated from the solid nodes, crossings from the
 // box edge.
 void base_sums(const uint8_t *mask, int nx, int ny, int periodic, const int *cv, double rho0,
-               double *link_base, double *flux_base)
+               double *link_base, double *flux_base, const std::vector<long long> *solids)
 {
+    std::vector<long long> own;
+    if (!solids) {
+        own = solid_nodes(mask, nx, ny);
+        solids = &own;
+    }
     const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     auto W = [](int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); };
@@ -100,7 +138,7 @@ void base_sums(const uint8_t *mask, int nx, int ny, int periodic, const int *cv,
         return true;
     };
     double lb[2] = {0, 0};
-    for (long long k : solid_nodes(mask, nx, ny)) {  // row-major, like a plain double loop
+    for (long long k : *solids) {  // row-major, like a plain double loop
         const int x = (int)(k % nx), y = (int)(k / nx);
         for (int i = 1; i < 9; ++i) {  // fluid x_f = s - c_i with x_f + c_i = s
             int xf = x - CX[i], yf = y - CY[i];
@@ -151,7 +189,8 @@ bool finite_all(const double *v, int n)
 }
 
 std::string check_domain(const uint8_t *mask, int nx, int ny, double tau, const double *u_in,
-                         int n_u_in, int periodic, const int *cv_in, int *cv_out)
+                         int n_u_in, int periodic, const int *cv_in, int *cv_out,
+                         const std::vector<long long> *solids)
 {
     char buf[256];
     if (!mask || !u_in) return "mask and u_in must not be NULL";
@@ -185,7 +224,7 @@ std::string check_domain(const uint8_t *mask, int nx, int ny, double tau, const 
     }
     int cv[4];
     if (!cv_in || cv_in[0] < 0) {
-        auto_cv(mask, nx, ny, periodic, cv);
+        auto_cv(mask, nx, ny, periodic, cv, solids);
     } else {
         memcpy(cv, cv_in, sizeof(cv));
         if (!range_ok(cv[0], cv[1], nx, periodic != 0) || !range_ok(cv[2], cv[3], ny, true)) {
