@@ -726,7 +726,7 @@ lbm_status lbm_create(const uint8_t *mask, int nx, int ny, double tau, const dou
         if (be != cudaSuccess) return fail(cuda_err(h, be, "boundary nodes"));
     }
     CKC(launch_init(h->storage, h->pop[0], h->plane, h->mask_d, nx, ny, h->pitch, h->u_row, h->rho0,
-                    h->inlet, s),
+                    h->inlet, s, n_u_in == 1),
         "initial state");
     CKC(cudaStreamSynchronize(s), "sync");
     h->launches = 7;

@@ -595,7 +595,7 @@ lbm_status lbm_batch_create(const lbm_domain *domains, int n, const lbm_bc *bc_i
         if (e == cudaSuccess)
             e = launch_init(b->storage, b->pop[0] + m.pop_off * (long long)b->elem, m.plane, b->mask_d + m.mask_off,
                             m.nx, m.ny, m.pitch, b->u_row + m.row_off, b->rho0,
-                            (char *)b->inlet + m.inlet_off * (long long)b->elem, s);
+                            (char *)b->inlet + m.inlet_off * (long long)b->elem, s, in.n_u_in == 1);
         if (e == cudaSuccess)
             e = launch_link_count(b->nbits + m.node_off, m.nx, m.ny, m.pitch, blk + blk_off, nb[d], s);
         if (e == cudaSuccess) e = launch_scan_blocks(blk + blk_off, nb[d], totals_d + d, s);

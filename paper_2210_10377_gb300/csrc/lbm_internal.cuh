@@ -212,9 +212,10 @@ cudaError_t launch_tile_flags(const uint16_t *nbits, int nx, int ny, int pitch, 
                               cudaStream_t st);
 int link_blocks(int nx, int ny);
 
+// uniform: every row has the same inlet velocity (one row is searched and copied)
 cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *mask, int nx,
                         int ny, int pitch, const double *u_row, double rho0, void *inlet,
-                        cudaStream_t st);
+                        cudaStream_t st, int uniform = 0);
 // tmap: the tensor map over the source buffer (staged kernel), or NULL
 cudaError_t launch_collide_stream(int storage, const StepArgs &a, int tiles_x, int tiles_y,
                                   bool momentum_only, const void *tmap, cudaStream_t st);

@@ -334,14 +334,15 @@ __device__ double as_double(__half v) { return (double)__half2float(v); }
 // components closest to the exact ones (sum of squared errors; ties go to the
 // choice nearer element by element).  FP64 storage stores the values as they are.
 template <int S>
-__global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int ny,
+__global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int ny, int rows,
                              typename Traits<S>::store_t *__restrict__ inlet)
 {
     using ST = typename Traits<S>::store_t;
-    // one warp per row; lane l tries the choices l, l + 32, ... of the 2^9
+    // one warp per row of the first `rows` (the table's rows are ny apart);
+    // lane l tries the choices l, l + 32, ... of the 2^9
     const int y = blockIdx.x * (blockDim.x / 32) + (int)(threadIdx.x / 32);
     const int lane = threadIdx.x & 31;
-    if (y >= ny) return;
+    if (y >= rows) return;
     const double u = u_row[y];
     double v[9];
 #pragma unroll
@@ -396,46 +397,53 @@ __global__ void k_inlet_rows(const double *__restrict__ u_row, double rho0, int 
     }
 }
 
-// Initial state: every fluid node of row y holds the row's inlet state.
+// Initial state: every fluid node of row y holds the row's inlet state.  With
+// a uniform inlet only row 0 of the table was computed: every row reads it,
+// and the thread at x = 0 of each other row copies it into its own row (no
+// thread writes row 0, so no read meets a write).
 template <int S>
 __global__ void k_init(typename Traits<S>::store_t *__restrict__ pop, long long plane,
                        const uint8_t *__restrict__ mask, int nx, int ny, int pitch,
-                       const typename Traits<S>::store_t *__restrict__ inlet)
+                       typename Traits<S>::store_t *__restrict__ inlet, int uniform)
 {
     using ST = typename Traits<S>::store_t;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     if (x >= nx) return;
+    const int ys = uniform ? 0 : y;
     bool solid = mask[(long long)y * nx + x] != 0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        pop[i * plane + (long long)y * pitch + x] =
-            solid ? to_store<ST>((typename Traits<S>::comp_t)0) : inlet[i * ny + y];
+    for (int i = 0; i < 9; ++i) {
+        const ST v = inlet[i * ny + ys];
+        pop[i * plane + (long long)y * pitch + x] = solid ? to_store<ST>((typename Traits<S>::comp_t)0) : v;
+        if (uniform && x == 0 && y > 0) inlet[i * ny + y] = v;
+    }
 }
 
 cudaError_t launch_init(int storage, void *pop, long long plane, const uint8_t *mask, int nx,
                         int ny, int pitch, const double *u_row, double rho0, void *inlet,
-                        cudaStream_t st)
+                        cudaStream_t st, int uniform)
 {
     dim3 grid((nx + 255) / 256, ny);
-    const int rb = (ny + 3) / 4;  // four rows (warps) a block
+    const int rows = uniform ? 1 : ny;  // a uniform inlet has one distinct row
+    const int rb = (rows + 3) / 4;      // four rows (warps) a block
     switch (storage) {
     case LBM_F64:
-        k_inlet_rows<LBM_F64><<<rb, 128, 0, st>>>(u_row, rho0, ny, (double *)inlet);
-        k_init<LBM_F64><<<grid, 256, 0, st>>>((double *)pop, plane, mask, nx, ny, pitch, (const double *)inlet);
+        k_inlet_rows<LBM_F64><<<rb, 128, 0, st>>>(u_row, rho0, ny, rows, (double *)inlet);
+        k_init<LBM_F64><<<grid, 256, 0, st>>>((double *)pop, plane, mask, nx, ny, pitch, (double *)inlet, uniform);
         break;
     case LBM_F32:
-        k_inlet_rows<LBM_F32><<<rb, 128, 0, st>>>(u_row, rho0, ny, (float *)inlet);
-        k_init<LBM_F32><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch, (const float *)inlet);
+        k_inlet_rows<LBM_F32><<<rb, 128, 0, st>>>(u_row, rho0, ny, rows, (float *)inlet);
+        k_init<LBM_F32><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch, (float *)inlet, uniform);
         break;
     case LBM_F32_DEV:
-        k_inlet_rows<LBM_F32_DEV><<<rb, 128, 0, st>>>(u_row, rho0, ny, (float *)inlet);
-        k_init<LBM_F32_DEV><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch, (const float *)inlet);
+        k_inlet_rows<LBM_F32_DEV><<<rb, 128, 0, st>>>(u_row, rho0, ny, rows, (float *)inlet);
+        k_init<LBM_F32_DEV><<<grid, 256, 0, st>>>((float *)pop, plane, mask, nx, ny, pitch, (float *)inlet, uniform);
         break;
     default:
-        k_inlet_rows<LBM_F16_DEV><<<rb, 128, 0, st>>>(u_row, rho0, ny, (__half *)inlet);
-        k_init<LBM_F16_DEV><<<grid, 256, 0, st>>>((__half *)pop, plane, mask, nx, ny, pitch,
-                                                   (const __half *)inlet);
+        k_inlet_rows<LBM_F16_DEV><<<rb, 128, 0, st>>>(u_row, rho0, ny, rows, (__half *)inlet);
+        k_init<LBM_F16_DEV><<<grid, 256, 0, st>>>((__half *)pop, plane, mask, nx, ny, pitch, (__half *)inlet,
+                                                   uniform);
         break;
     }
     return cudaGetLastError();
